@@ -1,0 +1,308 @@
+/*
+ * rsa_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, sequential CPU restatement of what the GPU path computes:
+ * random sequential adsorption (RSA) of linear k-mers on an L x L torus run
+ * to jamming, plus the k-mer count at which a wrapping cluster first appears.
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+ * leg may load this file's library.  It shares no code, header or table with
+ * the CUDA library, and it never calls it.
+ *
+ * Paper: Slutskii, Barash, Tarasevich, "Percolation and jamming of random
+ * sequential adsorption samples of large linear k-mers on a square lattice"
+ * (arXiv:1810.06800).
+ *
+ *   Model (Sec. I, Sec. II.A): L x L lattice with periodic boundaries (a
+ *   torus); a k-mer occupies k consecutive cells, horizontal or vertical;
+ *   deposition is RSA until jamming (no further k-mer fits).
+ *   Deposition (Sec. II.B): the viable-list form tries every (site,
+ *   orientation) candidate exactly once, in uniformly random order, and
+ *   accepts it iff all of its cells are free.  Here that random order is the
+ *   ascending order of 64-bit priorities key(idx) (see oracle_key below);
+ *   candidate idx = (o*L + y)*L + x, o = 0 horizontal, o = 1 vertical.
+ *   Cluster labelling (Sec. II.C): union-find over k-mers, the smaller
+ *   cluster is attached under the larger one (sizes are stored).
+ *   Percolation (Sec. II.D): a cluster wraps the torus in one or both
+ *   directions; found with per-node x/y displacements from the root
+ *   (Machta / Newman-Ziff).  This file uses the exact rule "an edge inside
+ *   one cluster whose lifted displacements disagree" and also evaluates the
+ *   paper's |x1-x2|+|y1-y2| > 2k test so the two can be compared.
+ *
+ * Everything is integer arithmetic; there is no floating point here.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- splitmix64 (Steele, Lea, Flood, OOPSLA 2014; Vigna's public-domain
+ * reference): state advances by the golden gamma 0x9E3779B97F4A7C15 and each
+ * output is the "Mix13" finaliser of the new state. ------------------------ */
+#define ORC_GAMMA 0x9E3779B97F4A7C15ULL
+
+uint64_t oracle_mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* Per-sample stream base: the first splitmix64 output for state `seed`. */
+uint64_t oracle_base(uint64_t seed) { return oracle_mix64(seed + ORC_GAMMA); }
+
+/* Priority of candidate idx: output number idx+1 of splitmix64 started at the
+ * sample base.  Smaller key = tried earlier. */
+uint64_t oracle_key(uint64_t base, uint64_t idx)
+{
+    return oracle_mix64(base + ORC_GAMMA * (idx + 1));
+}
+
+void oracle_keys(uint32_t L, uint64_t seed, uint64_t *keys)
+{
+    uint64_t n = 2ULL * L * L, b = oracle_base(seed);
+    for (uint64_t i = 0; i < n; ++i) keys[i] = oracle_key(b, i);
+}
+
+/* ---- sequential greedy scan (Sec. II.B) -------------------------------- */
+typedef struct { uint64_t key; uint32_t idx; } orc_pair;
+
+static int orc_cmp(const void *a, const void *b)
+{
+    const orc_pair *p = (const orc_pair *)a, *q = (const orc_pair *)b;
+    if (p->key < q->key) return -1;
+    if (p->key > q->key) return 1;
+    return (p->idx < q->idx) ? -1 : (p->idx > q->idx);
+}
+
+/* cell (row y, column x) of cell number i of candidate idx */
+static void orc_cell(uint32_t L, uint32_t idx, uint32_t i, uint32_t *y, uint32_t *x)
+{
+    uint32_t o = idx / (L * L), r = idx % (L * L);
+    uint32_t y0 = r / L, x0 = r % L;
+    if (o == 0) { *y = y0; *x = (x0 + i) % L; }
+    else        { *y = (y0 + i) % L; *x = x0; }
+}
+
+/* Scan the 2L^2 candidates in ascending key order; accept a candidate iff
+ * its k cells are free.  accepted[] receives the accepted idx in scan order.
+ * Returns n_j, or -1 if two keys are equal (the order would be undefined). */
+int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
+                    uint32_t *accepted, uint8_t *occ)
+{
+    uint64_t n = 2ULL * L * L;
+    orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
+    if (!p) return -2;
+    for (uint64_t i = 0; i < n; ++i) { p[i].key = keys[i]; p[i].idx = (uint32_t)i; }
+    qsort(p, n, sizeof(orc_pair), orc_cmp);
+    for (uint64_t i = 1; i < n; ++i)
+        if (p[i].key == p[i - 1].key) { free(p); return -1; }
+    memset(occ, 0, (size_t)L * L);
+    int64_t nj = 0;
+    for (uint64_t s = 0; s < n; ++s) {
+        uint32_t idx = p[s].idx, y, x, i, ok = 1;
+        for (i = 0; i < k && ok; ++i) {
+            orc_cell(L, idx, i, &y, &x);
+            if (occ[(size_t)y * L + x]) ok = 0;
+        }
+        if (!ok) continue;
+        for (i = 0; i < k; ++i) {
+            orc_cell(L, idx, i, &y, &x);
+            occ[(size_t)y * L + x] = 1;
+        }
+        accepted[nj++] = idx;
+    }
+    free(p);
+    return nj;
+}
+
+/* ---- union-find with displacement vectors (Sec. II.C, II.D) ------------ */
+typedef struct {
+    int32_t *parent;   /* parent k-mer (scan order), self for a root   */
+    int64_t *dx, *dy;  /* anchor of node minus anchor of parent (lift) */
+    int64_t *size;     /* cells in the cluster (valid at roots)         */
+} orc_uf;
+
+/* Root of m, and the lifted displacement of m's anchor from that root.
+ * Path compression keeps every stored displacement relative to the new
+ * parent. */
+static int32_t orc_find(orc_uf *u, int32_t m, int64_t *ox, int64_t *oy)
+{
+    int64_t sx = 0, sy = 0;
+    int32_t r = m;
+    while (u->parent[r] != r) { sx += u->dx[r]; sy += u->dy[r]; r = u->parent[r]; }
+    /* compress: walk again, re-pointing each node straight at r */
+    int64_t cx = sx, cy = sy;
+    int32_t v = m;
+    while (u->parent[v] != r && v != r) {
+        int32_t nxt = u->parent[v];
+        int64_t nx = cx - u->dx[v], ny = cy - u->dy[v];
+        u->parent[v] = r; u->dx[v] = cx; u->dy[v] = cy;
+        cx = nx; cy = ny; v = nxt;
+    }
+    *ox = sx; *oy = sy;
+    return r;
+}
+
+static int64_t orc_iabs(int64_t a) { return a < 0 ? -a : a; }
+
+/* Add accepted k-mers in scan order and return n_c: the number of k-mers
+ * on the lattice when a wrapping cluster first exists (0 if none does after
+ * all n_j).  *nc_paper receives the step at which the paper's test
+ * |x1-x2|+|y1-y2| > 2k (comparing the root displacements of two contact
+ * sites of one old cluster touched by the new k-mer) first fires.
+ *
+ * Exact rule: every lattice edge (a, a+d) between occupied cells is a
+ * constraint lift(a) + d = lift(a+d).  An edge whose two ends already share
+ * a root and whose displacements disagree closes a cycle of non-zero
+ * winding, i.e. the cluster wraps. */
+int64_t oracle_percolation(uint32_t L, uint32_t k, const uint32_t *accepted,
+                           int64_t nj, int64_t *nc_paper)
+{
+    size_t LL = (size_t)L * L;
+    int32_t *map = (int32_t *)malloc(LL * sizeof(int32_t));
+    orc_uf u;
+    u.parent = (int32_t *)malloc((size_t)(nj + 1) * sizeof(int32_t));
+    u.dx = (int64_t *)malloc((size_t)(nj + 1) * sizeof(int64_t));
+    u.dy = (int64_t *)malloc((size_t)(nj + 1) * sizeof(int64_t));
+    u.size = (int64_t *)malloc((size_t)(nj + 1) * sizeof(int64_t));
+    /* per new k-mer: the first contact site seen for each old root */
+    int32_t *c_root = (int32_t *)malloc((size_t)(4 * k + 4) * sizeof(int32_t));
+    int64_t *c_x = (int64_t *)malloc((size_t)(4 * k + 4) * sizeof(int64_t));
+    int64_t *c_y = (int64_t *)malloc((size_t)(4 * k + 4) * sizeof(int64_t));
+    if (!map || !u.parent || !u.dx || !u.dy || !u.size || !c_root || !c_x || !c_y) {
+        free(map); free(u.parent); free(u.dx); free(u.dy); free(u.size);
+        free(c_root); free(c_x); free(c_y);
+        if (nc_paper) *nc_paper = -2;
+        return -2;
+    }
+    for (size_t i = 0; i < LL; ++i) map[i] = -1;
+    int64_t nc = 0, ncp = 0;
+    static const int dirx[4] = {1, -1, 0, 0}, diry[4] = {0, 0, 1, -1};
+
+    for (int64_t m = 0; m < nj; ++m) {
+        uint32_t idx = accepted[m], o = idx / (uint32_t)LL;
+        uint32_t y0 = (idx % (uint32_t)LL) / L, x0 = idx % L;
+        int64_t ex = (o == 0), ey = (o == 1);   /* unit step along the k-mer */
+        u.parent[m] = (int32_t)m; u.dx[m] = 0; u.dy[m] = 0; u.size[m] = k;
+
+        /* (1) the paper's test, evaluated on the forest before m is merged */
+        int nroots = 0, paper_hit = 0;
+        for (uint32_t i = 0; i < k; ++i) {
+            uint32_t ay, ax; orc_cell(L, idx, i, &ay, &ax);
+            for (int d = 0; d < 4; ++d) {
+                uint32_t by = (uint32_t)(((int64_t)ay + diry[d] + L) % L);
+                uint32_t bx = (uint32_t)(((int64_t)ax + dirx[d] + L) % L);
+                int32_t mp = map[(size_t)by * L + bx];
+                if (mp < 0) continue;
+                uint32_t idp = accepted[mp], op = idp / (uint32_t)LL;
+                uint32_t yp = (idp % (uint32_t)LL) / L, xp = idp % L;
+                int64_t j = (op == 0) ? (int64_t)((bx + L - xp) % L)
+                                      : (int64_t)((by + L - yp) % L);
+                int64_t rx, ry;
+                int32_t r = orc_find(&u, mp, &rx, &ry);
+                int64_t sx = rx + j * (op == 0), sy = ry + j * (op == 1);
+                int c;
+                for (c = 0; c < nroots; ++c) if (c_root[c] == r) break;
+                if (c == nroots) { c_root[c] = r; c_x[c] = sx; c_y[c] = sy; ++nroots; }
+                else if (orc_iabs(sx - c_x[c]) + orc_iabs(sy - c_y[c]) > 2 * (int64_t)k)
+                    paper_hit = 1;
+            }
+        }
+
+        /* (2) place m, then process every lattice edge at each of its cells */
+        for (uint32_t i = 0; i < k; ++i) {
+            uint32_t ay, ax; orc_cell(L, idx, i, &ay, &ax);
+            map[(size_t)ay * L + ax] = (int32_t)m;
+        }
+        int wrap = 0;
+        for (uint32_t i = 0; i < k; ++i) {
+            uint32_t ay, ax; orc_cell(L, idx, i, &ay, &ax);
+            for (int d = 0; d < 4; ++d) {
+                uint32_t by = (uint32_t)(((int64_t)ay + diry[d] + L) % L);
+                uint32_t bx = (uint32_t)(((int64_t)ax + dirx[d] + L) % L);
+                int32_t mp = map[(size_t)by * L + bx];
+                if (mp < 0) continue;
+                uint32_t idp = accepted[mp], op = idp / (uint32_t)LL;
+                uint32_t yp = (idp % (uint32_t)LL) / L, xp = idp % L;
+                int64_t j = (op == 0) ? (int64_t)((bx + L - xp) % L)
+                                      : (int64_t)((by + L - yp) % L);
+                /* lift: anchor(mp) + j*e(mp) = anchor(m) + i*e(m) + d */
+                int64_t r1x, r1y, r2x, r2y;
+                int32_t r1 = orc_find(&u, (int32_t)m, &r1x, &r1y);
+                int32_t r2 = orc_find(&u, mp, &r2x, &r2y);
+                int64_t ax1 = r1x + (int64_t)i * ex + dirx[d];
+                int64_t ay1 = r1y + (int64_t)i * ey + diry[d];
+                int64_t bx2 = r2x + j * (op == 0), by2 = r2y + j * (op == 1);
+                if (r1 == r2) {
+                    if (ax1 != bx2 || ay1 != by2) wrap = 1;
+                } else {
+                    /* position of r2 relative to r1 */
+                    int64_t Dx = ax1 - bx2, Dy = ay1 - by2;
+                    if (u.size[r1] >= u.size[r2]) {
+                        u.parent[r2] = r1; u.dx[r2] = Dx; u.dy[r2] = Dy;
+                        u.size[r1] += u.size[r2];
+                    } else {
+                        u.parent[r1] = r2; u.dx[r1] = -Dx; u.dy[r1] = -Dy;
+                        u.size[r2] += u.size[r1];
+                    }
+                }
+            }
+        }
+        if (wrap && nc == 0) nc = m + 1;
+        if (paper_hit && ncp == 0) ncp = m + 1;
+        if (nc && ncp) break;
+    }
+    free(map); free(u.parent); free(u.dx); free(u.dy); free(u.size);
+    free(c_root); free(c_x); free(c_y);
+    if (nc_paper) *nc_paper = ncp;
+    return nc;
+}
+
+/* One sample from its seed: n_j and n_c.  Returns 0, or a negative code. */
+int oracle_sample(uint32_t L, uint32_t k, uint64_t seed, int64_t *nj, int64_t *nc,
+                  int64_t *nc_paper)
+{
+    size_t n = 2ULL * L * L;
+    uint64_t *keys = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint32_t *acc = (uint32_t *)malloc(((size_t)L * L / k + 1) * sizeof(uint32_t));
+    uint8_t *occ = (uint8_t *)malloc((size_t)L * L);
+    if (!keys || !acc || !occ) { free(keys); free(acc); free(occ); return -2; }
+    oracle_keys(L, seed, keys);
+    int64_t j = oracle_scan(L, k, keys, acc, occ);
+    int rc = 0;
+    if (j < 0) rc = (int)j;
+    else {
+        *nj = j;
+        *nc = oracle_percolation(L, k, acc, j, nc_paper);
+        if (*nc < 0) rc = (int)*nc;
+    }
+    free(keys); free(acc); free(occ);
+    return rc;
+}
+
+/* Same with caller-supplied keys (2L^2 distinct values). */
+int oracle_sample_keys(uint32_t L, uint32_t k, const uint64_t *keys, int64_t *nj,
+                       int64_t *nc, int64_t *nc_paper, uint32_t *accepted)
+{
+    uint8_t *occ = (uint8_t *)malloc((size_t)L * L);
+    if (!occ) return -2;
+    int64_t j = oracle_scan(L, k, keys, accepted, occ);
+    free(occ);
+    if (j < 0) return (int)j;
+    *nj = j;
+    *nc = oracle_percolation(L, k, accepted, j, nc_paper);
+    return *nc < 0 ? (int)*nc : 0;
+}
+
+/* Jamming check: 1 iff no candidate has all of its k cells free. */
+int oracle_is_jammed(uint32_t L, uint32_t k, const uint8_t *occ)
+{
+    for (uint32_t idx = 0; idx < 2u * L * L; ++idx) {
+        uint32_t i, y, x, free_all = 1;
+        for (i = 0; i < k && free_all; ++i) {
+            orc_cell(L, idx, i, &y, &x);
+            if (occ[(size_t)y * L + x]) free_all = 0;
+        }
+        if (free_all) return 0;
+    }
+    return 1;
+}
