@@ -1,0 +1,105 @@
+/*
+ * rsa.h -- C ABI of the GB300 library for random sequential adsorption (RSA)
+ * of linear k-mers on an L x L periodic square lattice.
+ *
+ * Model (arXiv:1810.06800, Sec. I and Sec. II.A): k-mers cover k consecutive
+ * cells, horizontal or vertical; deposition is RSA on a torus until jamming.
+ * Per sample the library returns
+ *   n_j -- the number of k-mers at jamming (p_j = k n_j / L^2, Sec. I), and
+ *   n_c -- the number of k-mers on the lattice when a cluster first wraps the
+ *          torus in one or both directions (p_c = k n_c / L^2, Sec. II.D).
+ *
+ * Deposition order: every (orientation o, row y, column x) placement is one
+ * candidate, idx = (o*L + y)*L + x (o = 0 horizontal, covering (y, x+i mod L);
+ * o = 1 vertical, covering (y+i mod L, x); i < k).  The viable-list form of
+ * RSA (Sec. II.B) tries each candidate once in uniformly random order; here
+ * that order is the ascending order of the 64-bit priority
+ *     key(idx) = mix64(base + 0x9E3779B97F4A7C15 * (idx + 1)),
+ *     base     = mix64(seed + 0x9E3779B97F4A7C15),
+ * mix64 being the splitmix64 output finaliser (Steele, Lea, Flood 2014).
+ * mix64 is a bijection, so the 2 L^2 keys of a sample are distinct.
+ *
+ * Conventions for every entry point:
+ *   - return 0 on success or a negative RSA_E* code; rsa_last_error() then
+ *     holds a message (thread-local, valid until the next call on the thread);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default);
+ *   - host pointers are caller-owned and only read/written during the call;
+ *   - no call traps the GPU: device-side failures are recorded in a status
+ *     word per sample and reported by rsa_results().
+ *   - 1 <= k <= L <= 32768.
+ */
+#ifndef RSA_GB300_H
+#define RSA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSA_OK        0
+#define RSA_EINVAL   (-1)  /* bad argument                                  */
+#define RSA_ENOMEM   (-2)  /* device allocation or bound workspace too small */
+#define RSA_ECUDA    (-3)  /* a CUDA runtime call failed                     */
+#define RSA_ETIMEOUT (-4)  /* a device loop hit its iteration cap            */
+#define RSA_ENOWRAP  (-5)  /* no wrapping cluster at jamming (contradicts the
+                              Appendix A Proposition; n_c = UINT32_MAX)      */
+#define RSA_ESTATE   (-6)  /* call out of order (e.g. results before a run)  */
+
+typedef struct rsa rsa_t;
+
+/* Create a handle for lattice size L, k-mer length k and base seed.  Sample
+ * i of rsa_run_batch uses seed + i.  Allocates no device memory yet.
+ * Errors: RSA_EINVAL unless 1 <= k <= L <= 32768 and out != NULL. */
+int rsa_create(uint32_t L, uint32_t k, uint64_t seed, rsa_t **out);
+
+/* Run n_samples samples (seeds seed .. seed + n_samples - 1) to jamming and
+ * find each first-wrap count, on `stream`.  Device memory is allocated on
+ * first use (or taken from a bound workspace).  The call returns once the
+ * work is enqueued; it synchronises `stream` a few times while running the
+ * data-dependent round and bisection loops.  Results stay on the device
+ * until rsa_results(). */
+int rsa_run_batch(rsa_t *h, uint32_t n_samples, void *stream);
+
+/* As rsa_run_batch with explicit per-sample seeds (host array of n). */
+int rsa_run_seeds(rsa_t *h, const uint64_t *seeds, uint32_t n, void *stream);
+
+/* TEST ONLY: one sample whose candidate order is given by the caller:
+ * keys[idx] for idx < 2 L^2 (host array), all distinct and != 2^64 - 1
+ * (RSA_EINVAL otherwise). */
+int rsa_run_keys(rsa_t *h, const uint64_t *keys, void *stream);
+
+/* Copy the last run's results to caller-owned host arrays of length n
+ * (n <= samples of the last run; either pointer may be NULL).  Synchronises
+ * the run's stream.  Returns the first per-sample error code, if any; a
+ * sample without a wrap has n_c = UINT32_MAX. */
+int rsa_results(rsa_t *h, uint32_t *n_j, uint32_t *n_c, uint32_t n);
+
+/* Per-sample diagnostics of the last run (any pointer may be NULL, arrays of
+ * length n): rounds of the parallel greedy, bisection probes, contact edges
+ * of the k-mer graph, and the status code. */
+int rsa_sample_stats(rsa_t *h, uint32_t *rounds, uint32_t *probes, uint32_t *edges,
+                     int32_t *status, uint32_t n);
+
+/* TEST ONLY: the accepted candidates (idx) of sample `sample` of the last run,
+ * sorted ascending; *count receives n_j; at most cap values are written. */
+int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_t *count);
+
+/* Bytes of device workspace a run of n_samples needs for (L, k). */
+int rsa_workspace_bytes(uint32_t L, uint32_t k, uint32_t n_samples, uint64_t *bytes);
+
+/* Use caller-owned device memory (e.g. a torch tensor) as the workspace;
+ * the library never frees it.  dev_ptr must be 256-byte aligned.  A run that
+ * needs more than `bytes` fails with RSA_ENOMEM.  Pass NULL to unbind. */
+int rsa_bind_workspace(rsa_t *h, void *dev_ptr, uint64_t bytes);
+
+/* Release the handle and any device memory the library allocated. */
+void rsa_destroy(rsa_t *h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *rsa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSA_GB300_H */

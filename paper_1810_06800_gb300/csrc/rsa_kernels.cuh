@@ -1,0 +1,492 @@
+// rsa_kernels.cuh -- round, contact-graph and bisection kernels (sm_103a).
+#pragma once
+#include "rsa_device.cuh"
+
+namespace rsak {
+
+// Launch geometry of the row pass: one warp per (row, segment of S cells).
+struct RowCfg {
+  u32 S, nseg;        // segment length, segments per row
+  u32 warps;          // warps per block
+  u32 warp_words;     // u64 words of per-warp scratch (A region + B region)
+  u32 nmax;           // max span length (S + k - 1)
+  int global_scratch; // 1: per-warp scratch in g.scratch instead of smem
+};
+
+// Geometry of the column pass: W adjacent columns x (segment of S rows).
+struct ColCfg {
+  u32 S, nseg;        // segment length (rows), segments per column
+  u32 W, nstrip;      // columns per block, column strips
+  u32 nmax, nocc;     // value span and occupancy span lengths
+  u32 block_words;    // u64 words of scratch per block
+  int global_scratch;
+};
+
+__device__ __forceinline__ u32 wrap_add(u32 a, u32 b, u32 L) {
+  u32 r = a + b;
+  return r >= L ? (r % L) : r;
+}
+
+// MODE 0: horizontal part of cmin.  For row y and x in the segment,
+//   cmin(y,x) = min over live horizontal candidates anchored at
+//               (y, x-k+1 .. x) of their key.
+// A horizontal candidate is live iff its k cells are free.
+// MODE 1: accept horizontal candidates: (y,x) is accepted iff
+//   min(cmin(y, x .. x+k-1)) == key(0, y, x).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_row(Group g, RowCfg rc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const u32 s = blockIdx.y;
+  if (g.st[s].done) return;
+  const u32 warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const u32 L = g.L, k = g.k;
+  u64* A;
+  if (rc.global_scratch)
+    A = g.scratch +
+        (((size_t)blockIdx.y * gridDim.x + blockIdx.x) * rc.warps + warp) * rc.warp_words;
+  else
+    A = reinterpret_cast<u64*>(smem_raw) + (size_t)warp * rc.warp_words;
+  u64* B = A + rc.nmax;          // values -> prefix minima
+  u32* N = reinterpret_cast<u32*>(A);  // next-occupied table (aliases A)
+  const u8* occ = g.occ + (size_t)s * g.LL;
+  u64* cmin = g.cmin + (size_t)s * g.LL;
+  bool any_alive = false;
+  const u64 total = (u64)L * rc.nseg;
+  for (u64 q = (u64)blockIdx.x * rc.warps + warp; q < total; q += (u64)gridDim.x * rc.warps) {
+    const u32 y = (u32)(q / rc.nseg), seg = (u32)(q % rc.nseg);
+    const u32 x0 = seg * rc.S;
+    const u32 Se = min(rc.S, L - x0);
+    const u32 n = Se + k - 1;
+    const u8* orow = occ + (size_t)y * L;
+    u64* crow = cmin + (size_t)y * L;
+    if (MODE == 0) {
+      const u32 xs = (x0 + L - (k - 1)) % L;
+      const u32 nocc = Se + 2 * k - 2;
+      for (u32 u = lane; u < nocc; u += 32) N[u] = orow[wrap_add(xs, u % L, L)] ? u : NONE32;
+      __syncwarp();
+      warp_scan_bwd<u32>(N, N, nocc, 0u, NONE32);
+      __syncwarp();
+      for (u32 u = lane; u < n; u += 32) {
+        const bool alive = N[u] >= u + k;  // NONE32 >= anything
+        u64 v = KEY_NONE;
+        if (alive) {
+          const u32 x = wrap_add(xs, u % L, L);
+          v = cand_key(g, s, (u64)y * L + x);
+          any_alive = true;
+        }
+        B[u] = v;
+      }
+    } else {
+      for (u32 u = lane; u < n; u += 32) B[u] = crow[wrap_add(x0, u % L, L)];
+    }
+    __syncwarp();
+    warp_scan_bwd<u64>(B, A, n, k, KEY_NONE);  // suffix minima -> A
+    __syncwarp();
+    warp_scan_fwd<u64>(B, B, n, k, KEY_NONE);  // prefix minima in place
+    __syncwarp();
+    for (u32 v = lane; v < Se; v += 32) {
+      const u64 w = tmin(A[v], B[v + k - 1]);
+      const u32 x = x0 + v;
+      if (MODE == 0) {
+        crow[x] = w;
+      } else if (w != KEY_NONE) {
+        const u32 idx = y * L + x;
+        if (w == cand_key(g, s, idx)) accept_candidate(g, s, idx, w);
+      }
+    }
+    __syncwarp();
+  }
+  if (MODE == 0) {
+    if (__any_sync(FULL, any_alive) && lane == 0) atomicOr(&g.st[s].alive, 1u);
+  }
+}
+
+// MODE 0: vertical part of cmin, combined with the horizontal part already
+//   in cmin: cmin(y,x) = min(cmin(y,x), min over live vertical candidates
+//   anchored at (y-k+1 .. y, x)).
+// MODE 1: accept vertical candidates: (y,x) accepted iff
+//   min(cmin(y .. y+k-1, x)) == key(1, y, x).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_col(Group g, ColCfg cc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const u32 s = blockIdx.y;
+  if (g.st[s].done) return;
+  const u32 L = g.L, k = g.k, W = cc.W, G = blockDim.x / W;
+  u64* base;
+  if (cc.global_scratch)
+    base = g.scratch + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * cc.block_words;
+  else
+    base = reinterpret_cast<u64*>(smem_raw);
+  u64* A = base;                                     // nmax*W (N aliases it)
+  const size_t a_words = max((size_t)cc.nmax * W, ((size_t)cc.nocc * W + 1) / 2);
+  u64* B = A + a_words;                              // nmax*W
+  u64* aggv = B + (size_t)cc.nmax * W;               // G*W
+  u8* aggf = reinterpret_cast<u8*>(aggv + (size_t)G * W);  // G*W
+  u32* N = reinterpret_cast<u32*>(A);
+  const u8* occ = g.occ + (size_t)s * g.LL;
+  u64* cmin = g.cmin + (size_t)s * g.LL;
+  bool any_alive = false;
+  const u32 total = cc.nstrip * cc.nseg;
+  for (u32 q = blockIdx.x; q < total; q += gridDim.x) {
+    const u32 strip = q / cc.nseg, seg = q % cc.nseg;
+    const u32 c0 = strip * W, y0 = seg * cc.S;
+    const u32 Se = min(cc.S, L - y0);
+    const u32 n = Se + k - 1;
+    if (MODE == 0) {
+      const u32 ys = (y0 + L - (k - 1)) % L;
+      const u32 nocc = Se + 2 * k - 2;
+      for (u32 f = threadIdx.x; f < nocc * W; f += blockDim.x) {
+        const u32 u = f / W, c = f % W, x = c0 + c;
+        u32 v = NONE32;
+        if (x < L && occ[(size_t)wrap_add(ys, u % L, L) * L + x]) v = u;
+        N[f] = v;
+      }
+      __syncthreads();
+      lines_scan_bwd<u32>(N, N, nocc, 0u, NONE32, W, reinterpret_cast<u32*>(aggv), aggf);
+      for (u32 f = threadIdx.x; f < n * W; f += blockDim.x) {
+        const u32 u = f / W, c = f % W, x = c0 + c;
+        u64 v = KEY_NONE;
+        if (x < L && N[f] >= u + k) {
+          const u32 y = wrap_add(ys, u % L, L);
+          v = cand_key(g, s, (u64)L * L + (u64)y * L + x);
+          any_alive = true;
+        }
+        B[f] = v;
+      }
+    } else {
+      for (u32 f = threadIdx.x; f < n * W; f += blockDim.x) {
+        const u32 u = f / W, c = f % W, x = c0 + c;
+        B[f] = x < L ? cmin[(size_t)wrap_add(y0, u % L, L) * L + x] : KEY_NONE;
+      }
+    }
+    __syncthreads();
+    lines_scan_bwd<u64>(B, A, n, k, KEY_NONE, W, aggv, aggf);
+    lines_scan_fwd<u64>(B, B, n, k, KEY_NONE, W, aggv, aggf);
+    for (u32 f = threadIdx.x; f < Se * W; f += blockDim.x) {
+      const u32 v = f / W, c = f % W, x = c0 + c;
+      if (x >= L) continue;
+      const u64 w = tmin(A[f], B[f + (size_t)(k - 1) * W]);
+      const u32 y = y0 + v;
+      if (MODE == 0) {
+        u64* p = cmin + (size_t)y * L + x;
+        *p = tmin(*p, w);
+      } else if (w != KEY_NONE) {
+        const u32 idx = (u32)(g.LL + (u64)y * L + x);
+        if (w == cand_key(g, s, idx)) accept_candidate(g, s, idx, w);
+      }
+    }
+    __syncthreads();
+  }
+  if (MODE == 0) {
+    if (__syncthreads_or(any_alive) && threadIdx.x == 0) atomicOr(&g.st[s].alive, 1u);
+  }
+}
+
+// Per-sample set-up: stream base from the seed, state cleared.
+__global__ void k_init(Group g, const u64* seeds) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  g.base[s] = mix64(seeds[s] + SM_GAMMA);
+  SampleState z = {};
+  g.st[s] = z;
+}
+
+// End of a round: a sample with no live candidate left is jammed.
+__global__ void k_round_end(Group g, u32 round_cap, u32* n_active) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  SampleState& st = g.st[s];
+  if (st.done) return;
+  if (!st.alive) {
+    st.done = 1;
+    return;
+  }
+  st.alive = 0;
+  st.rounds += 1;
+  if (st.rounds >= round_cap) {
+    st.status |= ST_ROUND_CAP;
+    st.done = 1;
+    return;
+  }
+  atomicAdd(n_active, 1u);
+}
+
+// ---------------------------------------------------------------------
+// Contact graph of the jammed lattice.  Nodes are accepted k-mers; a
+// lattice edge (a, a+e), e in {+x, +y}, between occupied cells of k-mers
+// m1 and m2 says that in the lift anchor(m2) = anchor(m1) + delta with
+//   delta = i e(m1) + e - j e(m2)  (i, j = positions of a, a+e inside the
+// k-mers).  Runs of identical (m1, m2, delta) along the direction
+// perpendicular to e are emitted once; a run start is forced at row 0 (for
+// +x) / column 0 (for +y) so that runs that close around the torus are kept.
+// Only edges whose m1 == m2 and delta == 0 (inside one k-mer) are dropped.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ u32 pos_in_kmer(u32 idx, u32 cy, u32 cx, u32 L, u32 LL, u32* o) {
+  const u32 oo = idx / LL, r = idx % LL;
+  const u32 y0 = r / L, x0 = r % L;
+  *o = oo;
+  return oo == 0 ? (cx + L - x0) % L : (cy + L - y0) % L;
+}
+
+__device__ __forceinline__ bool contact(const Group& g, u32 s, u32 y, u32 x, u32 dir, u32* m1,
+                                        u32* m2, u32* dxy) {
+  const u32 L = g.L;
+  const u32* own = g.owner + (size_t)s * g.LL;
+  const u32 a = own[(size_t)y * L + x];
+  if (a == NONE32) return false;
+  const u32 by = dir ? (y + 1 == L ? 0 : y + 1) : y;
+  const u32 bx = dir ? x : (x + 1 == L ? 0 : x + 1);
+  const u32 b = own[(size_t)by * L + bx];
+  if (b == NONE32) return false;
+  const u32* nidx = g.node_idx + (size_t)s * g.cap_nodes;
+  u32 o1, o2;
+  const u32 i = pos_in_kmer(nidx[a], y, x, L, (u32)g.LL, &o1);
+  const u32 j = pos_in_kmer(nidx[b], by, bx, L, (u32)g.LL, &o2);
+  const int dx = (o1 == 0 ? (int)i : 0) + (dir == 0) - (o2 == 0 ? (int)j : 0);
+  const int dy = (o1 == 1 ? (int)i : 0) + (dir == 1) - (o2 == 1 ? (int)j : 0);
+  *m1 = a;
+  *m2 = b;
+  *dxy = ((u32)dx & 0xFFFFu) | (((u32)dy & 0xFFFFu) << 16);
+  return !(a == b && dx == 0 && dy == 0);
+}
+
+__global__ void k_edges(Group g) {
+  const u32 s = blockIdx.y;
+  const u32 L = g.L;
+  SampleState& st = g.st[s];
+  const u64* nkey = g.node_key + (size_t)s * g.cap_nodes;
+  Edge* E = g.edges + (size_t)s * g.cap_edges;
+  for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < g.LL;
+       c += (u64)gridDim.x * blockDim.x) {
+    const u32 y = (u32)(c / L), x = (u32)(c % L);
+#pragma unroll
+    for (u32 dir = 0; dir < 2; ++dir) {
+      u32 m1, m2, d;
+      bool emit = contact(g, s, y, x, dir, &m1, &m2, &d);
+      if (emit) {
+        const bool force = dir == 0 ? (y == 0) : (x == 0);
+        if (!force) {
+          const u32 py = dir == 0 ? y - 1 : y, px = dir == 0 ? x : x - 1;
+          u32 p1, p2, pd;
+          if (contact(g, s, py, px, dir, &p1, &p2, &pd) && p1 == m1 && p2 == m2 && pd == d)
+            emit = false;
+        }
+      }
+      if (emit) {
+        const u32 e = atomicAdd(&st.n_edges, 1u);
+        if (e < g.cap_edges) {
+          Edge ed;
+          ed.time = max(nkey[m1], nkey[m2]);
+          ed.m1 = m1;
+          ed.m2 = m2;
+          ed.dxy = d;
+          ed.pad = 0;
+          E[e] = ed;
+        } else {
+          atomicOr(&st.status, ST_EDGE_OVF);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// First wrap by bisection over the accepted priorities (Sec. II.D).
+// wrap(T): does the graph of k-mers with key <= T contain a cycle of
+// non-zero winding?  It is monotone in T; n_c = #{keys <= T*} for the
+// smallest such accepted key T*.  Each probe starts from the union-find
+// state of the last non-wrapping threshold `lo` and adds only edges with
+// lo < time <= mid.  Union-find words: parent (bits 0-31) and the lifted
+// offset of the node from its parent, dx (32-47), dy (48-63), modulo 2^16.
+// A wrap is a cycle of primitive winding (a, b) times L; for L < 65536 its
+// offset is never 0 modulo 2^16, so 16-bit offsets decide exactly.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ u64 uf_pack(u32 p, u32 dx, u32 dy) {
+  return (u64)p | ((u64)(dx & 0xFFFFu) << 32) | ((u64)(dy & 0xFFFFu) << 48);
+}
+
+constexpr u32 UF_CAP = 1u << 20;
+
+// Root of x and x's offset from it.  Path halving by CAS; a failed CAS is
+// harmless because every stored (parent, offset) pair stays a true ancestor
+// relation.  Loads bypass L1 (other SMs write these words).
+__device__ __forceinline__ u32 uf_find(u64* W, u32 x, u32* ox, u32* oy, bool* capped) {
+  u32 sx = 0, sy = 0;
+  for (u32 it = 0; it < UF_CAP; ++it) {
+    const u64 wx = __ldcg(W + x);
+    const u32 p = (u32)wx;
+    if (p == x) {
+      *ox = sx;
+      *oy = sy;
+      return x;
+    }
+    const u64 wp = __ldcg(W + p);
+    const u32 gp = (u32)wp;
+    if (gp != p) {
+      const u64 nw = uf_pack(gp, (u32)(wx >> 32) + (u32)(wp >> 32),
+                             (u32)(wx >> 48) + (u32)(wp >> 48));
+      atomicCAS(W + x, wx, nw);
+    }
+    sx += (u32)(wx >> 32);
+    sy += (u32)(wx >> 48);
+    x = p;
+  }
+  *capped = true;
+  *ox = sx;
+  *oy = sy;
+  return x;
+}
+
+// Add edge "anchor(m2) = anchor(m1) + d"; returns true if it closes a cycle
+// of non-zero winding.  Roots are linked larger-id under smaller-id, so the
+// forest stays acyclic under concurrent unions.
+__device__ bool uf_union(u64* W, u32 m1, u32 m2, u32 dxy, bool* capped) {
+  const u32 dx = dxy & 0xFFFFu, dy = dxy >> 16;
+  for (u32 it = 0; it < UF_CAP; ++it) {
+    u32 o1x, o1y, o2x, o2y;
+    const u32 r1 = uf_find(W, m1, &o1x, &o1y, capped);
+    const u32 r2 = uf_find(W, m2, &o2x, &o2y, capped);
+    if (*capped) return false;
+    // lifted position of r2 minus r1
+    const u32 Dx = o1x + dx - o2x, Dy = o1y + dy - o2y;
+    if (r1 == r2) return ((Dx | Dy) & 0xFFFFu) != 0;
+    if (r1 < r2) {
+      if (atomicCAS(W + r2, uf_pack(r2, 0, 0), uf_pack(r1, Dx, Dy)) == uf_pack(r2, 0, 0))
+        return false;
+    } else {
+      if (atomicCAS(W + r1, uf_pack(r1, 0, 0), uf_pack(r2, 0u - Dx, 0u - Dy)) ==
+          uf_pack(r1, 0, 0))
+        return false;
+    }
+  }
+  *capped = true;
+  return false;
+}
+
+__global__ void k_search_init(Group g) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  SampleState& st = g.st[s];
+  st.lo = 0;
+  st.lo_valid = 0;
+  st.cnt_lo = 0;
+  st.hi = KEY_NONE;
+  st.cnt_hi = min(st.n_nodes, g.cap_nodes);
+  st.mid = KEY_NONE;  // first probe: the whole jammed lattice must wrap
+  st.hi_ok = 0;
+  st.cur = 0;
+  st.sdone = (st.status & (ST_NODE_OVF | ST_EDGE_OVF | ST_ROUND_CAP)) ? 1u : 0u;
+  st.nc = NONE32;
+  st.probes = 0;
+}
+
+__global__ void k_uf_identity(Group g) {
+  const u32 s = blockIdx.y;
+  const u32 nn = min(g.st[s].n_nodes, g.cap_nodes);
+  u64* U = g.uf + (size_t)s * 2 * g.cap_nodes;
+  for (u32 m = blockIdx.x * blockDim.x + threadIdx.x; m < nn; m += gridDim.x * blockDim.x)
+    U[m] = uf_pack(m, 0, 0);
+}
+
+// Working copy of the union-find state at `lo`.
+__global__ void k_probe_copy(Group g) {
+  const u32 s = blockIdx.y;
+  SampleState& st = g.st[s];
+  if (st.sdone) return;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st.wrap = 0;
+    st.cnt_mid = 0;
+  }
+  const u32 nn = min(st.n_nodes, g.cap_nodes);
+  const u64* S = g.uf + ((size_t)s * 2 + st.cur) * g.cap_nodes;
+  u64* Wd = g.uf + ((size_t)s * 2 + (st.cur ^ 1u)) * g.cap_nodes;
+  for (u32 m = blockIdx.x * blockDim.x + threadIdx.x; m < nn; m += gridDim.x * blockDim.x)
+    Wd[m] = S[m];
+}
+
+__global__ void k_probe(Group g) {
+  const u32 s = blockIdx.y;
+  SampleState& st = g.st[s];
+  if (st.sdone) return;
+  const u64 lo = st.lo, mid = st.mid;
+  const bool lo_valid = st.lo_valid != 0;
+  const u32 nn = min(st.n_nodes, g.cap_nodes);
+  const u32 ne = min(st.n_edges, g.cap_edges);
+  u64* Wd = g.uf + ((size_t)s * 2 + (st.cur ^ 1u)) * g.cap_nodes;
+  const Edge* E = g.edges + (size_t)s * g.cap_edges;
+  const u64* nkey = g.node_key + (size_t)s * g.cap_nodes;
+  bool wrap = false, capped = false;
+  u32 cnt = 0;
+  const u32 stride = gridDim.x * blockDim.x;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += stride) {
+    const Edge e = E[i];
+    if (e.time > mid || (lo_valid && e.time <= lo)) continue;
+    if (uf_union(Wd, e.m1, e.m2, e.dxy, &capped)) wrap = true;
+  }
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride)
+    cnt += nkey[i] <= mid;
+  // block reductions
+  const bool bw = __syncthreads_or(wrap);
+  const bool bc = __syncthreads_or(capped);
+  cnt = __reduce_add_sync(FULL, cnt);
+  __shared__ u32 part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u32 t = 0;
+    for (u32 w = 0; w < (blockDim.x + 31) / 32; ++w) t += part[w];
+    if (t) atomicAdd(&st.cnt_mid, t);
+    if (bw) atomicOr(&st.wrap, 1u);
+    if (bc) atomicOr(&st.status, ST_UF_CAP);
+  }
+}
+
+__global__ void k_search_decide(Group g, u32 probe_cap, u32* n_open) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.n) return;
+  SampleState& st = g.st[s];
+  if (st.sdone) return;
+  st.probes += 1;
+  if (st.status & ST_UF_CAP) {
+    st.sdone = 1;
+    return;
+  }
+  const bool w = st.wrap != 0;
+  if (!st.hi_ok) {
+    if (!w) {
+      st.status |= ST_NOWRAP;
+      st.nc = NONE32;
+      st.sdone = 1;
+      return;
+    }
+    st.hi_ok = 1;
+    st.cnt_hi = st.cnt_mid;
+  } else if (w) {
+    st.hi = st.mid;
+    st.cnt_hi = st.cnt_mid;
+  } else {
+    st.lo = st.mid;
+    st.lo_valid = 1;
+    st.cnt_lo = st.cnt_mid;
+    st.cur ^= 1u;
+  }
+  if (st.cnt_hi <= st.cnt_lo) {
+    st.status |= ST_SEARCH_BAD;
+    st.sdone = 1;
+    return;
+  }
+  if (st.cnt_hi - st.cnt_lo == 1) {
+    st.nc = st.cnt_hi;
+    st.sdone = 1;
+    return;
+  }
+  if (st.probes >= probe_cap) {
+    st.status |= ST_SEARCH_CAP;
+    st.sdone = 1;
+    return;
+  }
+  st.mid = st.lo_valid ? st.lo + (st.hi - st.lo) / 2 : st.hi / 2;
+  atomicAdd(n_open, 1u);
+}
+
+}  // namespace rsak

@@ -1,0 +1,190 @@
+"""Python binding of the C ABI in ``include/rsa.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_lib/librsa_gb300.so``;
+this module never computes any part of it.  If the library is missing the
+first call raises, so nothing can silently fall back to the CPU.
+PyTorch is used only for the CUDA stream and, optionally, for device memory
+bound as the library's workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RSA_OK, RSA_EINVAL, RSA_ENOMEM, RSA_ECUDA, RSA_ETIMEOUT, RSA_ENOWRAP, RSA_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6)
+_NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_ECUDA",
+          RSA_ETIMEOUT: "RSA_ETIMEOUT", RSA_ENOWRAP: "RSA_ENOWRAP", RSA_ESTATE: "RSA_ESTATE"}
+SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_results",
+           "rsa_sample_stats", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
+           "rsa_destroy", "rsa_last_error"]
+
+_lib = None
+
+
+class RSAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing: run "
+                           "paper_1810_06800_gb300.build.build() (or __graft_entry__.build())")
+    lib = ctypes.CDLL(_build.LIB)
+    u32, u64, vp, ip = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+    lib.rsa_create.argtypes = [u32, u32, u64, ctypes.POINTER(vp)]
+    lib.rsa_run_batch.argtypes = [vp, u32, vp]
+    lib.rsa_run_seeds.argtypes = [vp, vp, u32, vp]
+    lib.rsa_run_keys.argtypes = [vp, vp, vp]
+    lib.rsa_results.argtypes = [vp, vp, vp, u32]
+    lib.rsa_sample_stats.argtypes = [vp, vp, vp, vp, vp, u32]
+    lib.rsa_accepted.argtypes = [vp, u32, vp, u32, ctypes.POINTER(u32)]
+    lib.rsa_workspace_bytes.argtypes = [u32, u32, u32, ctypes.POINTER(u64)]
+    lib.rsa_bind_workspace.argtypes = [vp, vp, u64]
+    lib.rsa_destroy.argtypes = [vp]
+    lib.rsa_destroy.restype = None
+    lib.rsa_last_error.argtypes = []
+    lib.rsa_last_error.restype = ctypes.c_char_p
+    for name in SYMBOLS[:-2]:
+        getattr(lib, name).restype = ip
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RSAError(rc, load().rsa_last_error().decode())
+    return rc
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def rsa_create(L: int, k: int, seed: int = 1):
+    h = ctypes.c_void_p()
+    _check(load().rsa_create(L, k, seed & (2**64 - 1), ctypes.byref(h)))
+    return h
+
+
+def rsa_run_batch(h, n_samples: int, stream=None):
+    return _check(load().rsa_run_batch(h, n_samples, _stream_ptr(stream)))
+
+
+def rsa_run_seeds(h, seeds, stream=None):
+    a = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    return _check(load().rsa_run_seeds(h, a.ctypes.data, a.size, _stream_ptr(stream)))
+
+
+def rsa_run_keys(h, keys, stream=None):
+    a = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
+    return _check(load().rsa_run_keys(h, a.ctypes.data, _stream_ptr(stream)))
+
+
+def rsa_results(h, n: int, check: bool = True):
+    nj = np.zeros(n, dtype=np.uint32)
+    nc = np.zeros(n, dtype=np.uint32)
+    rc = load().rsa_results(h, nj.ctypes.data, nc.ctypes.data, n)
+    if check:
+        _check(rc)
+    return nj, nc
+
+
+def rsa_sample_stats(h, n: int):
+    r = np.zeros(n, dtype=np.uint32)
+    p = np.zeros(n, dtype=np.uint32)
+    e = np.zeros(n, dtype=np.uint32)
+    s = np.zeros(n, dtype=np.int32)
+    _check(load().rsa_sample_stats(h, r.ctypes.data, p.ctypes.data, e.ctypes.data,
+                                   s.ctypes.data, n))
+    return dict(rounds=r, probes=p, edges=e, status=s)
+
+
+def rsa_accepted(h, sample: int):
+    cnt = ctypes.c_uint32()
+    _check(load().rsa_accepted(h, sample, None, 0, ctypes.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), dtype=np.uint32)
+    _check(load().rsa_accepted(h, sample, out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def rsa_workspace_bytes(L: int, k: int, n_samples: int) -> int:
+    b = ctypes.c_uint64()
+    _check(load().rsa_workspace_bytes(L, k, n_samples, ctypes.byref(b)))
+    return int(b.value)
+
+
+def rsa_bind_workspace(h, tensor_or_ptr, nbytes: int | None = None):
+    if tensor_or_ptr is None:
+        return _check(load().rsa_bind_workspace(h, None, 0))
+    if hasattr(tensor_or_ptr, "data_ptr"):
+        ptr = tensor_or_ptr.data_ptr()
+        nbytes = tensor_or_ptr.numel() * tensor_or_ptr.element_size()
+    else:
+        ptr = int(tensor_or_ptr)
+    return _check(load().rsa_bind_workspace(h, ctypes.c_void_p(ptr), int(nbytes)))
+
+
+def rsa_destroy(h):
+    if h is not None and h.value:
+        load().rsa_destroy(h)
+
+
+def rsa_last_error() -> str:
+    return load().rsa_last_error().decode()
+
+
+class Lattice:
+    """Convenience owner of one handle: ``Lattice(L, k).run(seeds)``."""
+
+    def __init__(self, L: int, k: int, seed: int = 1):
+        self.L, self.k = L, k
+        self.h = rsa_create(L, k, seed)
+
+    def run(self, seeds, stream=None):
+        seeds = np.asarray(seeds, dtype=np.uint64)
+        rsa_run_seeds(self.h, seeds, stream)
+        return rsa_results(self.h, seeds.size)
+
+    def run_keys(self, keys, stream=None):
+        rsa_run_keys(self.h, keys, stream)
+        return rsa_results(self.h, 1)
+
+    def stats(self, n):
+        return rsa_sample_stats(self.h, n)
+
+    def accepted(self, sample=0):
+        return rsa_accepted(self.h, sample)
+
+    def close(self):
+        rsa_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if self.h is not None:
+                self.close()
+        except Exception:
+            pass

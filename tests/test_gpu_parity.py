@@ -1,0 +1,163 @@
+"""GPU path vs the CPU oracle through the C ABI: n_j and n_c must be
+bit-exact per sample, and the jammed configuration (the set of accepted
+candidates) identical.  Sizes span several tiles and ragged tails; edge cases
+cover L = 1, k = 1, k = L, lattices smaller than one tile, caller-supplied
+adversarial priority orders and the long-window code path."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_06800_gb300 import rsa, workloads
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+def _oracle_many(L, k, seeds):
+    nj, nc = oracle.samples(L, k, seeds, threads=THREADS)
+    return nj.astype(np.uint32), nc.astype(np.uint32)
+
+
+def _check(L, k, seeds, configs=0):
+    lat = rsa.Lattice(L, k)
+    nj, nc = lat.run(seeds)
+    wj, wc = _oracle_many(L, k, seeds)
+    assert np.array_equal(nj, wj), (L, k, nj, wj)
+    assert np.array_equal(nc, wc), (L, k, nc, wc)
+    for i in range(min(configs, len(seeds))):
+        want, _ = oracle.scan(L, k, oracle.keys(L, int(seeds[i])))
+        assert np.array_equal(lat.accepted(i), np.sort(want))
+    lat.close()
+    return nj, nc
+
+
+def test_plain_small_config_all_seeds():
+    w = workloads.PLAIN_SMALL
+    _check(w["L"], w["k"], w["seeds"], configs=10)
+
+
+@pytest.mark.parametrize("L,k", [(1, 1), (2, 1), (2, 2), (3, 1), (3, 2), (3, 3), (4, 4), (5, 2),
+                                 (7, 3), (8, 8), (9, 4), (16, 1), (16, 5), (31, 7), (33, 32),
+                                 (40, 4), (64, 64), (65, 2), (100, 3), (128, 8)])
+def test_small_and_ragged_shapes(L, k):
+    _check(L, k, list(range(1, 13)), configs=3)
+
+
+@pytest.mark.parametrize("L,k", [(256, 64), (300, 17), (512, 2), (777, 100), (1024, 1)])
+def test_medium_shapes(L, k):
+    _check(L, k, list(range(11, 15)), configs=1)
+
+
+def test_scale_config_sampled_seeds():
+    # L = 1024, k = 32 in one batch of 64 samples; the oracle checks all
+    w = workloads.PLAIN_SCALE
+    seeds = w["seeds"][:64]
+    _check(w["L"], w["k"], seeds, configs=2)
+
+
+@pytest.mark.parametrize("L,k", [(1024, 512), (2048, 1024), (4100, 2050)])
+def test_long_windows(L, k):
+    _check(L, k, [3, 4], configs=1)
+
+
+def test_batch_results_do_not_depend_on_batch_mix():
+    L, k = 128, 8
+    seeds = list(range(1, 41))
+    lat = rsa.Lattice(L, k)
+    nj_all, nc_all = lat.run(seeds)
+    nj_a, nc_a = lat.run(seeds[:7])
+    nj_b, nc_b = lat.run(seeds[7:])
+    assert np.array_equal(nj_all, np.concatenate([nj_a, nj_b]))
+    assert np.array_equal(nc_all, np.concatenate([nc_a, nc_b]))
+    lat.close()
+
+
+def test_run_batch_uses_consecutive_seeds():
+    L, k = 64, 4
+    h = rsa.rsa_create(L, k, 77)
+    rsa.rsa_run_batch(h, 5)
+    nj, nc = rsa.rsa_results(h, 5)
+    wj, wc = _oracle_many(L, k, range(77, 82))
+    assert np.array_equal(nj, wj) and np.array_equal(nc, wc)
+    rsa.rsa_destroy(h)
+
+
+@pytest.mark.parametrize("L,k", [(6, 2), (16, 3), (24, 4), (32, 8)])
+@pytest.mark.parametrize("kind", ["perm", "monotone", "descending", "wide"])
+def test_caller_keys(L, k, kind):
+    if kind == "perm":
+        keys = workloads.permutation_keys(L, 5)
+    elif kind == "monotone":
+        keys = workloads.monotone_keys(L)
+    elif kind == "descending":
+        keys = workloads.monotone_keys(L, descending=True)
+    else:
+        keys = workloads.wide_keys(L, 9)
+    lat = rsa.Lattice(L, k)
+    nj, nc = lat.run_keys(keys)
+    wj, wc, _, acc = oracle.sample_keys(L, k, keys)
+    assert int(nj[0]) == wj and int(nc[0]) == wc
+    assert np.array_equal(lat.accepted(0), np.sort(acc))
+    lat.close()
+
+
+def test_caller_keys_rejects_duplicates_and_sentinel():
+    L, k = 4, 2
+    lat = rsa.Lattice(L, k)
+    keys = workloads.permutation_keys(L, 1)
+    keys[3] = keys[4]
+    with pytest.raises(rsa.RSAError) as e:
+        lat.run_keys(keys)
+    assert e.value.code == rsa.RSA_EINVAL
+    keys = workloads.permutation_keys(L, 1)
+    keys[0] = np.uint64(2**64 - 1)
+    with pytest.raises(rsa.RSAError):
+        lat.run_keys(keys)
+    lat.close()
+
+
+def test_full_ring_lattice_long_window_path():
+    # k = L: the first k-mer is a ring (wraps alone) and fills its whole
+    # orientation: n_j = L, n_c = 1.  L = 8192 exceeds shared memory for the
+    # window, so this runs the global-scratch code path.
+    L = 8192
+    lat = rsa.Lattice(L, L)
+    nj, nc = lat.run([1, 2])
+    assert nj.tolist() == [L, L] and nc.tolist() == [1, 1]
+    lat.close()
+
+
+def test_bound_workspace_from_torch():
+    import torch
+    L, k, n = 64, 4, 6
+    nb = rsa.rsa_workspace_bytes(L, k, n)
+    buf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    h = rsa.rsa_create(L, k, 1)
+    rsa.rsa_bind_workspace(h, buf)
+    rsa.rsa_run_seeds(h, list(range(1, n + 1)))
+    nj, nc = rsa.rsa_results(h, n)
+    wj, wc = _oracle_many(L, k, range(1, n + 1))
+    assert np.array_equal(nj, wj) and np.array_equal(nc, wc)
+    small = torch.empty(nb // 2, dtype=torch.uint8, device="cuda")
+    rsa.rsa_bind_workspace(h, small)
+    with pytest.raises(rsa.RSAError) as e:
+        rsa.rsa_run_seeds(h, list(range(1, n + 1)))
+    assert e.value.code == rsa.RSA_ENOMEM
+    rsa.rsa_destroy(h)
+
+
+def test_invariants_at_scale():
+    # L = 1024, k = 32: every sample wraps no later than jamming, the
+    # statistics sit near Table I (k = 32: p_c 0.4733, p_j 0.6892 at L/k=100)
+    L, k = 1024, 32
+    lat = rsa.Lattice(L, k)
+    nj, nc = lat.run(list(range(1, 257)))
+    st = lat.stats(256)
+    assert np.all(st["status"] == 0)
+    assert np.all(nc >= 1) and np.all(nc <= nj)
+    pj, pc = k * nj / L**2, k * nc / L**2
+    assert abs(pj.mean() - 0.6892) < 0.01
+    assert abs(pc.mean() - 0.4733) < 0.05
+    lat.close()
