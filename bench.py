@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: jammed RSA samples per second on one GB300.
+
+Workload (default): L = 1024 periodic lattice, k = 32, 1000 samples with
+seeds 1..1000 per step (per rank under torchrun; rank r uses seeds
+r*1000 + 1 ..).  One step runs the whole path for the batch: the parallel
+greedy rounds to jamming (n_j), the contact graph, and the first-wrap
+bisection (n_c).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (a plain sequential scan plus
+union-find in C) on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "L1024_k32_x1000": dict(L=1024, k=32, n=1000),
+    "L64_k4_x100": dict(L=64, k=4, n=100),
+}
+METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
+# algorithmic bytes per lattice cell and per launch of each round kernel
+# (the design doc derives them): cell-min passes read occupancy (1 B) and write or
+# read-modify-write the 8-byte cell minimum; acceptance passes read it.
+BYTES_PER_CELL = {"k_row_cmin": 9, "k_col_cmin": 17, "k_row_accept": 8, "k_col_accept": 8}
+
+
+def src_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1810_06800_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_rate(L, k, seeds, budget_s, threads):
+    """Samples/s of the oracle on `threads` host threads over a bounded
+    prefix of the seeds (grown until it takes at least budget_s)."""
+    import oracle
+    done, t_total, m = 0, 0.0, max(1, threads)
+    while True:
+        chunk = seeds[done:done + m]
+        if not chunk:
+            break
+        t0 = time.perf_counter()
+        oracle.samples(L, k, chunk, threads=threads)
+        t_total += time.perf_counter() - t0
+        done += len(chunk)
+        if t_total >= budget_s:
+            break
+        m = min(2 * m, len(seeds) - done) or m
+    return done / t_total, done, t_total
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    L, k, n = wl["L"], wl["k"], wl["n"]
+    cores = os.cpu_count() or 1
+    seeds = list(range(1, n + 1))
+    per_step = min(n, 2 * cores)
+    for w in range(args.warmup):
+        oracle.samples(L, k, seeds[:per_step], threads=cores)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        lo = (s * per_step) % n
+        oracle.samples(L, k, (seeds + seeds)[lo:lo + per_step], threads=cores)
+    dt = time.perf_counter() - t0
+    rate = per_step * args.steps / dt
+    sample = f"{per_step} seeds of {args.workload} per step on {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "L": L, "k": k, "samples_per_step": per_step},
+        "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="L1024_k32_x1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, wl, world, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_1810_06800_gb300 import rsa
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    L, k, n = wl["L"], wl["k"], wl["n"]
+    seeds = np.arange(rank * n + 1, rank * n + n + 1, dtype=np.uint64)
+    stream = torch.cuda.current_stream()
+    lat = rsa.Lattice(L, k)
+    h = lat.h
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        rsa.rsa_run_seeds(h, seeds, stream)
+    torch.cuda.synchronize()
+    rsa.rsa_kernel_stats(h)  # reset counters
+
+    # ---- device-timed region (inputs resident: seeds + workspace) ----
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    rsa.rsa_profile(h, True)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rsa.rsa_run_seeds(h, seeds, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kstats = rsa.rsa_kernel_stats(h)
+    rsa.rsa_profile(h, False)
+    st = rsa.rsa_sample_stats(h, n)
+    nj, nc = rsa.rsa_results(h, n)
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n * world * args.steps / (ms / 1e3)
+
+    # ---- end-to-end through the C ABI with host buffers ----
+    nj_h = np.zeros(n, dtype=np.uint32)
+    nc_h = np.zeros(n, dtype=np.uint32)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        seeds_h = np.ascontiguousarray(seeds)  # host input, copied to HBM in the call
+        rsa.rsa_run_seeds(h, seeds_h, stream)
+        nj_h, nc_h = rsa.rsa_results(h, n)     # device -> host results
+    barrier()
+    wall = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([wall], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        wall = float(t.item())
+    e2e = n * world * args.steps / wall
+    assert np.array_equal(nj_h, nj) and np.array_equal(nc_h, nc)
+
+    if rank != 0:
+        lat.close()
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (CUDA events over the timed region) ----
+    ours = {name: v for name, v in kstats.items() if v[1] > 0}
+    dom = max(ours, key=lambda nm: ours[nm][0])
+    dom_ms, dom_launches = ours[dom]
+    passes = int(np.sum(st["rounds"].astype(np.int64) + 1)) * args.steps
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if dom in BYTES_PER_CELL:
+        alg_bytes = BYTES_PER_CELL[dom] * passes * L * L
+        achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+        if os.path.exists(tp):
+            with open(tp) as f:
+                tj = json.load(f)
+            ent = tj.get(dom)
+            if ent and ent.get("src") == src_digest():
+                traffic = ent["bytes_per_cell"] * (passes * L * L) / dom_launches
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "alg_bytes_per_launch": alg_bytes / dom_launches}
+    else:
+        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": peak,
+                "unit": "GB/s", "frac": None, "traffic": None}
+    kernel_table = {nm: {"ms": round(v[0], 3), "launches": v[1],
+                         "share": round(v[0] / sum(x[0] for x in ours.values()), 4)}
+                    for nm, v in ours.items()}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cores = os.cpu_count() or 1
+        rate, m, secs = cpu_oracle_rate(L, k, [int(s) for s in seeds], args.cpu_seconds, cores)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {m} seeds of {args.workload} ({secs:.1f} s on {cores} threads)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "L": L, "k": k, "samples_per_step": n,
+                   "seeds": f"rank*{n}+1..rank*{n}+{n}",
+                   "l2": "working set %.1f GB per step > 129 MB L2" % (
+                       rsa.rsa_workspace_bytes(L, k, n) / 1e9),
+                   "parallelism": f"samples sharded over {world} GPU(s), no collective"},
+        "sites_per_s": value * L * L,
+        "e2e": {"value": e2e, "unit": "samples/s", "h2d_bytes_per_step": int(8 * n),
+                "d2h_bytes_per_step": int(128 * n)},
+        "gpu_launches": int(sum(v[1] for v in ours.values())),
+        "roofline": roof,
+        "kernels": kernel_table,
+        "clocks": ck,
+        "cpu_baseline": cpu,
+        "stats": {"rounds_mean": float(st["rounds"].mean()),
+                  "probes_mean": float(st["probes"].mean()),
+                  "edges_mean": float(st["edges"].mean()),
+                  "p_j_mean": float((k * nj / L / L).mean()),
+                  "p_c_mean": float((k * nc / L / L).mean())},
+    }
+    print(json.dumps(out), flush=True)
+    lat.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -85,6 +85,17 @@ int rsa_sample_stats(rsa_t *h, uint32_t *rounds, uint32_t *probes, uint32_t *edg
  * sorted ascending; *count receives n_j; at most cap values are written. */
 int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_t *count);
 
+/* Measurement support (no counterpart in the paper).  rsa_profile(h, 1)
+ * makes later runs record a CUDA event pair around every kernel launch on
+ * the run's stream; rsa_kernel_stats() synchronises that stream and returns,
+ * per kernel kind i < n_kinds, the summed device time in ms[i] and the
+ * number of launches in launches[i] since the previous call, then resets
+ * both (launch counts are kept even with profiling off).  rsa_kernel_name(i)
+ * names kind i ("" past the last kind). */
+int rsa_profile(rsa_t *h, int enable);
+int rsa_kernel_stats(rsa_t *h, double *ms, unsigned long long *launches, uint32_t n_kinds);
+const char *rsa_kernel_name(uint32_t kind);
+
 /* Bytes of device workspace a run of n_samples needs for (L, k). */
 int rsa_workspace_bytes(uint32_t L, uint32_t k, uint32_t n_samples, uint64_t *bytes);
 

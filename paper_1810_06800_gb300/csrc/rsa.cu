@@ -16,6 +16,7 @@
 
 #include "../../include/rsa.h"
 #include "rsa_kernels.cuh"
+#include "rsa_tile.cuh"
 
 using namespace rsak;
 
@@ -44,11 +45,14 @@ constexpr size_t SMEM_BUDGET = 160 * 1024;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t occ, owner, cmin, base, node_key, node_idx, uf, edges, st, seeds, counters, keys,
+  size_t occ, occw, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
+      ebkt, nkey_b, nbkt, st, seeds, counters, keys,
       scratch, total;
 };
 
 struct Geometry {
+  bool tile;                    // power-of-two k <= 32 and L % 32 == 0
+  TileCfg tc;                   // (items filled per run)
   RowCfg row;
   ColCfg col;
   u32 row_threads, col_threads;
@@ -64,8 +68,13 @@ u32 cap_edges_of(u32 L, u32 k) {
   return (u32)c;
 }
 
+bool tile_shape(u32 L, u32 k) { return k <= 32 && (k & (k - 1)) == 0 && L % 32 == 0; }
+
 Geometry plan(u32 L, u32 k) {
   Geometry G{};
+  G.tile = tile_shape(L, k);
+  G.tc.T = L / 32;
+  G.tc.T2 = G.tc.T * G.tc.T;
   // ---- row pass: one warp per (row, segment) ----
   RowCfg& r = G.row;
   r.S = L <= 4096 ? L : 4096;
@@ -132,20 +141,27 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
     off = align_up(off + bytes);
     return at;
   };
-  l.occ = take(n * LL);
+  l.occ = take(G.tile ? 0 : n * LL);
+  l.occw = take(G.tile ? n * LL / 8 : 0);
+  l.dead = take(G.tile ? (size_t)n * G.tc.T2 : 0);
   l.owner = take(n * LL * 4);
   l.cmin = take(n * LL * 8);
   l.base = take((size_t)n * 8);
   l.node_key = take(n * cn * 8);
   l.node_idx = take(n * cn * 4);
+  l.node_pos = take(n * cn * 4);
   l.uf = take(n * cn * 16);
   l.edges = take(n * ce * sizeof(Edge));
+  l.edges_b = take(n * ce * sizeof(Edge));
+  l.ebkt = take((size_t)n * (NBKT + 1) * 4);
+  l.nkey_b = take(n * cn * 8);
+  l.nbkt = take((size_t)n * (NBKT + 1) * 4);
   l.st = take((size_t)n * sizeof(SampleState));
   l.seeds = take((size_t)n * 8);
   l.counters = take(64);
   l.keys = take(with_keys ? 2 * LL * 8 : 0);
   // scratch blocks are indexed by (sample, block) in the kernels
-  l.scratch = take(G.scratch_words * 8 * n);
+  l.scratch = take(G.tile ? 0 : G.scratch_words * 8 * n);
   l.total = off;
   return l;
 }
@@ -158,6 +174,25 @@ int set_smem(F* fn, size_t bytes) {
 }
 
 }  // namespace
+
+enum Kind {
+  KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
+  KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE, KD_COUNT
+};
+const char* const kKindNames[KD_COUNT] = {
+    "k_init",         "k_row_cmin",    "k_col_cmin",   "k_row_accept", "k_col_accept",
+    "k_tile_cmin",    "k_tile_accept", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
+    "k_probe_copy",   "k_probe",       "k_search_decide"};
+
+// Optional per-kernel timing with CUDA events recorded around each launch
+// on the launch stream, plus launch counts (always kept).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kinds;  // kind of record i uses events 2i, 2i+1
+  unsigned long long launches[KD_COUNT] = {};
+  double ms[KD_COUNT] = {};
+};
 
 struct rsa {
   u32 L, k;
@@ -177,6 +212,9 @@ struct rsa {
   cudaStream_t stream = nullptr;
   u32* h_counter = nullptr;  // pinned
   int device = -1;
+  int sm_count = 0;
+  int tile_blocks[2] = {0, 0};  // resident blocks per SM: cmin, accept
+  Prof prof;
 };
 
 namespace {
@@ -225,11 +263,46 @@ Group group_of(rsa_t* h, u32 n) {
   g.keys = h->with_keys ? reinterpret_cast<const u64*>(b + l.keys) : nullptr;
   g.node_key = reinterpret_cast<u64*>(b + l.node_key);
   g.node_idx = reinterpret_cast<u32*>(b + l.node_idx);
+  g.node_pos = reinterpret_cast<u32*>(b + l.node_pos);
+  g.edges_b = reinterpret_cast<Edge*>(b + l.edges_b);
+  g.ebkt = reinterpret_cast<u32*>(b + l.ebkt);
+  g.nkey_b = reinterpret_cast<u64*>(b + l.nkey_b);
+  g.nbkt = reinterpret_cast<u32*>(b + l.nbkt);
   g.uf = reinterpret_cast<u64*>(b + l.uf);
   g.edges = reinterpret_cast<Edge*>(b + l.edges);
   g.st = reinterpret_cast<SampleState*>(b + l.st);
   g.scratch = reinterpret_cast<u64*>(b + l.scratch);
   return g;
+}
+
+cudaEvent_t prof_event(Prof& p, size_t i) {
+  while (p.pool.size() <= i) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p.pool.push_back(e);
+  }
+  return p.pool[i];
+}
+
+// Launch wrapper: counts launches and, when profiling is on, brackets the
+// launch with two events on its stream.
+template <typename K, typename... Args>
+void launch(rsa_t* h, int kind, K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+            Args... args) {
+  Prof& p = h->prof;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (p.on) {
+    size_t i = p.kinds.size();
+    e0 = prof_event(p, 2 * i);
+    e1 = prof_event(p, 2 * i + 1);
+    if (e0 && e1) {
+      cudaEventRecord(e0, st);
+      p.kinds.push_back(kind);
+    }
+  }
+  kernel<<<grid, block, smem, st>>>(args...);
+  if (e0 && e1) cudaEventRecord(e1, st);
+  p.launches[kind] += 1;
 }
 
 int launch_check(const char* what) {
@@ -242,6 +315,53 @@ int read_counter(rsa_t* h, u32* dev_counter, u32* out) {
   CUDA_TRY(cudaMemcpyAsync(h->h_counter, dev_counter, 4, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   *out = *h->h_counter;
+  return 0;
+}
+
+template <int K>
+int tile_occ_k(rsa_t* h) {
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[0], k_tile_cmin<K>, 64, 0));
+  CUDA_TRY(
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[1], k_tile_accept<K>, 64, 0));
+  return 0;
+}
+
+int tile_occupancy(rsa_t* h) {
+  if (h->sm_count) return 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
+  int rc = 0;
+  switch (h->k) {
+    case 1: rc = tile_occ_k<1>(h); break;
+    case 2: rc = tile_occ_k<2>(h); break;
+    case 4: rc = tile_occ_k<4>(h); break;
+    case 8: rc = tile_occ_k<8>(h); break;
+    case 16: rc = tile_occ_k<16>(h); break;
+    default: rc = tile_occ_k<32>(h); break;
+  }
+  if (rc) return rc;
+  for (int i = 0; i < 2; ++i) h->tile_blocks[i] = std::max(1, h->tile_blocks[i]);
+  return 0;
+}
+
+template <int K>
+void launch_tile_k(rsa_t* h, Group g, TileCfg tc, u32* occw, u8* dead, const u32* tgrid,
+                   cudaStream_t stream) {
+  launch(h, KD_TILE_CMIN, k_tile_cmin<K>, dim3(tgrid[0]), dim3(64), 0, stream, g, tc, occw, dead);
+  launch(h, KD_TILE_ACCEPT, k_tile_accept<K>, dim3(tgrid[1]), dim3(64), 0, stream, g, tc, occw,
+         (const u8*)dead);
+}
+
+int launch_tile(rsa_t* h, Group g, TileCfg tc, u32* occw, u8* dead, const u32* tgrid,
+                cudaStream_t stream) {
+  switch (h->k) {
+    case 1: launch_tile_k<1>(h, g, tc, occw, dead, tgrid, stream); break;
+    case 2: launch_tile_k<2>(h, g, tc, occw, dead, tgrid, stream); break;
+    case 4: launch_tile_k<4>(h, g, tc, occw, dead, tgrid, stream); break;
+    case 8: launch_tile_k<8>(h, g, tc, occw, dead, tgrid, stream); break;
+    case 16: launch_tile_k<16>(h, g, tc, occw, dead, tgrid, stream); break;
+    case 32: launch_tile_k<32>(h, g, tc, occw, dead, tgrid, stream); break;
+    default: return fail(RSA_EINVAL, "tile path needs k in {1,2,4,8,16,32}");
+  }
   return 0;
 }
 
@@ -265,26 +385,49 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, (size_t)n * 8, cudaMemcpyHostToDevice, stream));
   if (keys)
     CUDA_TRY(cudaMemcpyAsync(b + l.keys, keys, 2 * LL * 8, cudaMemcpyHostToDevice, stream));
-  CUDA_TRY(cudaMemsetAsync(g.occ, 0, (size_t)n * LL, stream));
+  if (G.tile) {
+    CUDA_TRY(cudaMemsetAsync(b + l.occw, 0, (size_t)n * LL / 8, stream));
+    CUDA_TRY(cudaMemsetAsync(b + l.dead, 0, (size_t)n * G.tc.T2, stream));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(g.occ, 0, (size_t)n * LL, stream));
+  }
   CUDA_TRY(cudaMemsetAsync(g.owner, 0xFF, (size_t)n * LL * 4, stream));
-  k_init<<<(n + 127) / 128, 128, 0, stream>>>(g, d_seeds);
+  launch(h, KD_INIT, k_init, dim3((n + 127) / 128), dim3(128), 0, stream, g,
+         (const u64*)d_seeds);
   if ((rc = launch_check("k_init"))) return rc;
 
-  if ((rc = set_smem(k_row<0>, G.row_smem))) return rc;
-  if ((rc = set_smem(k_row<1>, G.row_smem))) return rc;
-  if ((rc = set_smem(k_col<0>, G.col_smem))) return rc;
-  if ((rc = set_smem(k_col<1>, G.col_smem))) return rc;
+  if (!G.tile) {
+    if ((rc = set_smem(k_row<0>, G.row_smem))) return rc;
+    if ((rc = set_smem(k_row<1>, G.row_smem))) return rc;
+    if ((rc = set_smem(k_col<0>, G.col_smem))) return rc;
+    if ((rc = set_smem(k_col<1>, G.col_smem))) return rc;
+  }
   const dim3 rg(G.row_grid_x.x, n), cg(G.col_grid_x.x, n);
+  TileCfg tc = G.tc;
+  tc.items = (u64)n * tc.T2;
+  u32* occw = reinterpret_cast<u32*>(b + l.occw);
+  u8* dead = reinterpret_cast<u8*>(b + l.dead);
+  u32 tgrid[2] = {0, 0};
+  if (G.tile) {
+    if ((rc = tile_occupancy(h))) return rc;
+    for (int i = 0; i < 2; ++i)
+      tgrid[i] = (u32)std::min<u64>(tc.items, (u64)h->sm_count * h->tile_blocks[i]);
+  }
   // every round accepts at least the smallest live key, so n_j + 1 rounds
   // always suffice
   const u32 round_cap = cap_nodes_of(h->L, h->k) + 2;
   for (u32 r = 0;; ++r) {
     CUDA_TRY(cudaMemsetAsync(d_counter, 0, 4, stream));
-    k_row<0><<<rg, G.row_threads, G.row_smem, stream>>>(g, G.row);
-    k_col<0><<<cg, G.col_threads, G.col_smem, stream>>>(g, G.col);
-    k_row<1><<<rg, G.row_threads, G.row_smem, stream>>>(g, G.row);
-    k_col<1><<<cg, G.col_threads, G.col_smem, stream>>>(g, G.col);
-    k_round_end<<<(n + 127) / 128, 128, 0, stream>>>(g, round_cap, d_counter);
+    if (G.tile) {
+      if ((rc = launch_tile(h, g, tc, occw, dead, tgrid, stream))) return rc;
+    } else {
+      launch(h, KD_ROW_CMIN, k_row<0>, rg, dim3(G.row_threads), G.row_smem, stream, g, G.row);
+      launch(h, KD_COL_CMIN, k_col<0>, cg, dim3(G.col_threads), G.col_smem, stream, g, G.col);
+      launch(h, KD_ROW_ACCEPT, k_row<1>, rg, dim3(G.row_threads), G.row_smem, stream, g, G.row);
+      launch(h, KD_COL_ACCEPT, k_col<1>, cg, dim3(G.col_threads), G.col_smem, stream, g, G.col);
+    }
+    launch(h, KD_ROUND_END, k_round_end, dim3((n + 127) / 128), dim3(128), 0, stream, g,
+           round_cap, d_counter);
     if ((rc = launch_check("round kernels"))) return rc;
     if ((r + 1) % ROUND_CHECK == 0) {
       u32 active;
@@ -295,23 +438,27 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   // contact graph of the jammed lattice
   {
     u32 bx = (u32)std::min<u64>((LL + 255) / 256, 4096);
-    k_edges<<<dim3(bx, n), 256, 0, stream>>>(g);
+    launch(h, KD_EDGES, k_edges, dim3(bx, n), dim3(256), 0, stream, g);
     if ((rc = launch_check("k_edges"))) return rc;
   }
+  launch(h, KD_BUCKET, k_bucket, dim3(n), dim3(1024), 0, stream, g);
   // bisection for the first wrap
-  k_search_init<<<(n + 127) / 128, 128, 0, stream>>>(g);
+  launch(h, KD_SEARCH_INIT, k_search_init, dim3((n + 127) / 128), dim3(128), 0, stream, g);
   {
     u32 bx = (u32)std::min<u64>(((u64)g.cap_nodes + 255) / 256, 1024);
-    k_uf_identity<<<dim3(bx, n), 256, 0, stream>>>(g);
+    launch(h, KD_SEARCH_INIT, k_uf_identity, dim3(bx, n), dim3(256), 0, stream, g);
   }
   if ((rc = launch_check("search init"))) return rc;
-  const u32 copy_bx = (u32)std::min<u64>(((u64)g.cap_nodes + 255) / 256, 1024);
-  const u32 probe_bx = (u32)std::min<u64>(((u64)g.cap_edges + 255) / 256, 512);
+  // enough blocks per sample to fill the GPU across the batch, no more
+  const u64 per_sample = std::max<u64>(8, 16384 / n);
+  const u32 copy_bx = (u32)std::min<u64>(((u64)g.cap_nodes + 255) / 256, per_sample);
+  const u32 probe_bx = (u32)std::min<u64>(((u64)g.cap_edges + 255) / 256, per_sample);
   for (u32 p = 0; p < PROBE_CAP + 1; ++p) {
     CUDA_TRY(cudaMemsetAsync(d_counter + 1, 0, 4, stream));
-    k_probe_copy<<<dim3(copy_bx, n), 256, 0, stream>>>(g);
-    k_probe<<<dim3(probe_bx, n), 256, 0, stream>>>(g);
-    k_search_decide<<<(n + 127) / 128, 128, 0, stream>>>(g, PROBE_CAP, d_counter + 1);
+    launch(h, KD_PROBE_COPY, k_probe_copy, dim3(copy_bx, n), dim3(256), 0, stream, g);
+    launch(h, KD_PROBE, k_probe, dim3(probe_bx, n), dim3(256), 0, stream, g);
+    launch(h, KD_DECIDE, k_search_decide, dim3((n + 127) / 128), dim3(128), 0, stream, g,
+           (u32)PROBE_CAP, d_counter + 1);
     if ((rc = launch_check("probe kernels"))) return rc;
     if ((p + 1) % PROBE_CHECK == 0) {
       u32 open;
@@ -456,8 +603,40 @@ int rsa_bind_workspace(rsa_t* h, void* dev_ptr, uint64_t bytes) {
   return 0;
 }
 
+int rsa_profile(rsa_t* h, int enable) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  h->prof.on = enable != 0;
+  return 0;
+}
+
+int rsa_kernel_stats(rsa_t* h, double* ms, unsigned long long* launches, uint32_t n_kinds) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  Prof& p = h->prof;
+  if (!p.kinds.empty()) {
+    if (h->stream || h->device >= 0) CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < p.kinds.size(); ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.pool[2 * i], p.pool[2 * i + 1]) == cudaSuccess)
+        p.ms[p.kinds[i]] += t;
+    }
+    p.kinds.clear();
+  }
+  for (uint32_t i = 0; i < n_kinds && i < (uint32_t)KD_COUNT; ++i) {
+    if (ms) ms[i] = p.ms[i];
+    if (launches) launches[i] = p.launches[i];
+    p.ms[i] = 0.0;
+    p.launches[i] = 0;
+  }
+  return 0;
+}
+
+const char* rsa_kernel_name(uint32_t kind) {
+  return kind < (uint32_t)KD_COUNT ? kKindNames[kind] : "";
+}
+
 void rsa_destroy(rsa_t* h) {
   if (!h) return;
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   if (h->own_ptr) cudaFree(h->own_ptr);
   if (h->h_counter) cudaFreeHost(h->h_counter);
   delete h;

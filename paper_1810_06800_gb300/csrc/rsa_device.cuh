@@ -33,6 +33,7 @@ constexpr u64 KEY_NONE = 0xFFFFFFFFFFFFFFFFull;  // dead / no candidate
 constexpr u64 SM_GAMMA = 0x9E3779B97F4A7C15ull;  // splitmix64 increment
 constexpr u32 NONE32 = 0xFFFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr u32 NBKT = 256;  // time buckets (top 8 bits of a priority)
 
 // status bits (per sample), mapped to RSA_E* codes by the host
 constexpr u32 ST_NODE_OVF = 1u;     // more accepted k-mers than L^2/k (bug)
@@ -77,8 +78,13 @@ struct Group {         // one batch of samples sharing (L, k)
   const u64* keys;     // caller priorities [2 L^2] (test path), else null
   u64* node_key;       // [n][cap_nodes]
   u32* node_idx;       // [n][cap_nodes]  accepted candidate idx
+  u32* node_pos;       // [n][cap_nodes]  o << 31 | y0 << 15 | x0 of the anchor
   u64* uf;             // [n][2][cap_nodes] union-find words
   Edge* edges;         // [n][cap_edges]
+  Edge* edges_b;       // [n][cap_edges] edges grouped by time >> 56
+  u32* ebkt;           // [n][NBKT + 1] bucket offsets into edges_b
+  u64* nkey_b;         // [n][cap_nodes] node keys grouped by key >> 56
+  u32* nbkt;           // [n][NBKT + 1] bucket offsets into nkey_b
   SampleState* st;     // [n]
   u64* scratch;        // global scratch for very long windows (or null)
 };
@@ -238,6 +244,7 @@ __device__ __forceinline__ void accept_candidate(const Group& g, u32 s, u32 idx,
   const u32 L = g.L;
   const u32 o = idx / (u32)g.LL, r = idx % (u32)g.LL;
   const u32 y0 = r / L, x0 = r % L;
+  g.node_pos[(size_t)s * g.cap_nodes + node] = (o << 31) | (y0 << 15) | x0;
   u8* occ = g.occ + (size_t)s * g.LL;
   u32* own = g.owner + (size_t)s * g.LL;
   if (o == 0) {

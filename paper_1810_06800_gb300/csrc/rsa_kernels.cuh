@@ -221,11 +221,13 @@ __global__ void k_round_end(Group g, u32 round_cap, u32* n_active) {
 // +x) / column 0 (for +y) so that runs that close around the torus are kept.
 // Only edges whose m1 == m2 and delta == 0 (inside one k-mer) are dropped.
 // ---------------------------------------------------------------------
-__device__ __forceinline__ u32 pos_in_kmer(u32 idx, u32 cy, u32 cx, u32 L, u32 LL, u32* o) {
-  const u32 oo = idx / LL, r = idx % LL;
-  const u32 y0 = r / L, x0 = r % L;
+// Position of cell (cy, cx) inside the k-mer whose anchor is packed as
+// o << 31 | y0 << 15 | x0; *o receives the orientation.
+__device__ __forceinline__ u32 pos_in_kmer(u32 pos, u32 cy, u32 cx, u32 L, u32* o) {
+  const u32 oo = pos >> 31, y0 = (pos >> 15) & 0x7FFFu, x0 = pos & 0x7FFFu;
   *o = oo;
-  return oo == 0 ? (cx + L - x0) % L : (cy + L - y0) % L;
+  const u32 d = oo == 0 ? cx - x0 : cy - y0;
+  return (int)d < 0 ? d + L : d;
 }
 
 __device__ __forceinline__ bool contact(const Group& g, u32 s, u32 y, u32 x, u32 dir, u32* m1,
@@ -238,10 +240,10 @@ __device__ __forceinline__ bool contact(const Group& g, u32 s, u32 y, u32 x, u32
   const u32 bx = dir ? x : (x + 1 == L ? 0 : x + 1);
   const u32 b = own[(size_t)by * L + bx];
   if (b == NONE32) return false;
-  const u32* nidx = g.node_idx + (size_t)s * g.cap_nodes;
+  const u32* npos = g.node_pos + (size_t)s * g.cap_nodes;
   u32 o1, o2;
-  const u32 i = pos_in_kmer(nidx[a], y, x, L, (u32)g.LL, &o1);
-  const u32 j = pos_in_kmer(nidx[b], by, bx, L, (u32)g.LL, &o2);
+  const u32 i = pos_in_kmer(npos[a], y, x, L, &o1);
+  const u32 j = pos_in_kmer(npos[b], by, bx, L, &o2);
   const int dx = (o1 == 0 ? (int)i : 0) + (dir == 0) - (o2 == 0 ? (int)j : 0);
   const int dy = (o1 == 1 ? (int)i : 0) + (dir == 1) - (o2 == 1 ? (int)j : 0);
   *m1 = a;
@@ -253,16 +255,21 @@ __device__ __forceinline__ bool contact(const Group& g, u32 s, u32 y, u32 x, u32
 __global__ void k_edges(Group g) {
   const u32 s = blockIdx.y;
   const u32 L = g.L;
+  const u32 lane = threadIdx.x & 31;
   SampleState& st = g.st[s];
   const u64* nkey = g.node_key + (size_t)s * g.cap_nodes;
   Edge* E = g.edges + (size_t)s * g.cap_edges;
-  for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < g.LL;
-       c += (u64)gridDim.x * blockDim.x) {
-    const u32 y = (u32)(c / L), x = (u32)(c % L);
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same number of iterations (ballots below)
+  const u64 iters = (g.LL + stride - 1) / stride;
+  for (u64 it = 0; it < iters; ++it) {
+    const u64 c = it * stride + (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool inb = c < g.LL;
+    const u32 y = inb ? (u32)(c / L) : 0, x = inb ? (u32)(c % L) : 0;
 #pragma unroll
     for (u32 dir = 0; dir < 2; ++dir) {
-      u32 m1, m2, d;
-      bool emit = contact(g, s, y, x, dir, &m1, &m2, &d);
+      u32 m1 = 0, m2 = 0, d = 0;
+      bool emit = inb && contact(g, s, y, x, dir, &m1, &m2, &d);
       if (emit) {
         const bool force = dir == 0 ? (y == 0) : (x == 0);
         if (!force) {
@@ -272,8 +279,14 @@ __global__ void k_edges(Group g) {
             emit = false;
         }
       }
+      const u32 mask = __ballot_sync(FULL, emit);
+      if (!mask) continue;
+      u32 basei = 0;
+      const u32 leader = __ffs(mask) - 1;
+      if (lane == leader) basei = atomicAdd(&st.n_edges, (u32)__popc(mask));
+      basei = __shfl_sync(FULL, basei, leader);
       if (emit) {
-        const u32 e = atomicAdd(&st.n_edges, 1u);
+        const u32 e = basei + __popc(mask & ((1u << lane) - 1u));
         if (e < g.cap_edges) {
           Edge ed;
           ed.time = max(nkey[m1], nkey[m2]);
@@ -287,6 +300,45 @@ __global__ void k_edges(Group g) {
         }
       }
     }
+  }
+}
+
+// Group one sample's edges by time >> 56 and its node keys by key >> 56
+// (counting sort into NBKT buckets), so that a bisection probe touches only
+// the edges whose time can lie in its window.  One block per sample.
+__global__ void __launch_bounds__(1024) k_bucket(Group g) {
+  __shared__ u32 he[NBKT], hn[NBKT], ce[NBKT], cn[NBKT];
+  const u32 s = blockIdx.x;
+  SampleState& st = g.st[s];
+  const u32 ne = min(st.n_edges, g.cap_edges), nn = min(st.n_nodes, g.cap_nodes);
+  const Edge* E = g.edges + (size_t)s * g.cap_edges;
+  Edge* E2 = g.edges_b + (size_t)s * g.cap_edges;
+  const u64* K = g.node_key + (size_t)s * g.cap_nodes;
+  u64* K2 = g.nkey_b + (size_t)s * g.cap_nodes;
+  u32* eb = g.ebkt + (size_t)s * (NBKT + 1);
+  u32* nb = g.nbkt + (size_t)s * (NBKT + 1);
+  for (u32 i = threadIdx.x; i < NBKT; i += blockDim.x) he[i] = hn[i] = 0;
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < ne; i += blockDim.x) atomicAdd(&he[(u32)(E[i].time >> 56)], 1u);
+  for (u32 i = threadIdx.x; i < nn; i += blockDim.x) atomicAdd(&hn[(u32)(K[i] >> 56)], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u32 a = 0, b = 0;
+    for (u32 i = 0; i < NBKT; ++i) {
+      eb[i] = a; ce[i] = a; a += he[i];
+      nb[i] = b; cn[i] = b; b += hn[i];
+    }
+    eb[NBKT] = a;
+    nb[NBKT] = b;
+  }
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < ne; i += blockDim.x) {
+    const Edge e = E[i];
+    E2[atomicAdd(&ce[(u32)(e.time >> 56)], 1u)] = e;
+  }
+  for (u32 i = threadIdx.x; i < nn; i += blockDim.x) {
+    const u64 kk = K[i];
+    K2[atomicAdd(&cn[(u32)(kk >> 56)], 1u)] = kk;
   }
 }
 
@@ -410,20 +462,23 @@ __global__ void k_probe(Group g) {
   if (st.sdone) return;
   const u64 lo = st.lo, mid = st.mid;
   const bool lo_valid = st.lo_valid != 0;
-  const u32 nn = min(st.n_nodes, g.cap_nodes);
-  const u32 ne = min(st.n_edges, g.cap_edges);
+  const u32* eb = g.ebkt + (size_t)s * (NBKT + 1);
+  const u32* nb = g.nbkt + (size_t)s * (NBKT + 1);
+  const u32 blo = lo_valid ? (u32)(lo >> 56) : 0u, bmid = (u32)(mid >> 56);
+  const u32 e0 = eb[blo], e1 = eb[bmid + 1];
+  const u32 n0 = nb[bmid], n1 = nb[bmid + 1];
   u64* Wd = g.uf + ((size_t)s * 2 + (st.cur ^ 1u)) * g.cap_nodes;
-  const Edge* E = g.edges + (size_t)s * g.cap_edges;
-  const u64* nkey = g.node_key + (size_t)s * g.cap_nodes;
+  const Edge* E = g.edges_b + (size_t)s * g.cap_edges;
+  const u64* nkey = g.nkey_b + (size_t)s * g.cap_nodes;
   bool wrap = false, capped = false;
   u32 cnt = 0;
   const u32 stride = gridDim.x * blockDim.x;
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += stride) {
+  for (u32 i = e0 + blockIdx.x * blockDim.x + threadIdx.x; i < e1; i += stride) {
     const Edge e = E[i];
     if (e.time > mid || (lo_valid && e.time <= lo)) continue;
     if (uf_union(Wd, e.m1, e.m2, e.dxy, &capped)) wrap = true;
   }
-  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += stride)
+  for (u32 i = n0 + blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride)
     cnt += nkey[i] <= mid;
   // block reductions
   const bool bw = __syncthreads_or(wrap);
@@ -433,7 +488,7 @@ __global__ void k_probe(Group g) {
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
   __syncthreads();
   if (threadIdx.x == 0) {
-    u32 t = 0;
+    u32 t = blockIdx.x == 0 ? n0 : 0u;  // all nodes of the buckets below mid's
     for (u32 w = 0; w < (blockDim.x + 31) / 32; ++w) t += part[w];
     if (t) atomicAdd(&st.cnt_mid, t);
     if (bw) atomicOr(&st.wrap, 1u);

@@ -21,7 +21,8 @@ _NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_EC
           RSA_ETIMEOUT: "RSA_ETIMEOUT", RSA_ENOWRAP: "RSA_ENOWRAP", RSA_ESTATE: "RSA_ESTATE"}
 SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_results",
            "rsa_sample_stats", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
-           "rsa_destroy", "rsa_last_error"]
+           "rsa_profile", "rsa_kernel_stats", "rsa_destroy", "rsa_kernel_name",
+           "rsa_last_error"]
 
 _lib = None
 
@@ -57,9 +58,13 @@ def load():
     lib.rsa_bind_workspace.argtypes = [vp, vp, u64]
     lib.rsa_destroy.argtypes = [vp]
     lib.rsa_destroy.restype = None
+    lib.rsa_profile.argtypes = [vp, ip]
+    lib.rsa_kernel_stats.argtypes = [vp, vp, vp, u32]
+    lib.rsa_kernel_name.argtypes = [u32]
+    lib.rsa_kernel_name.restype = ctypes.c_char_p
     lib.rsa_last_error.argtypes = []
     lib.rsa_last_error.restype = ctypes.c_char_p
-    for name in SYMBOLS[:-2]:
+    for name in SYMBOLS[:-3]:
         getattr(lib, name).restype = ip
     _lib = lib
     return lib
@@ -145,6 +150,25 @@ def rsa_bind_workspace(h, tensor_or_ptr, nbytes: int | None = None):
     else:
         ptr = int(tensor_or_ptr)
     return _check(load().rsa_bind_workspace(h, ctypes.c_void_p(ptr), int(nbytes)))
+
+
+def rsa_profile(h, enable: bool = True):
+    return _check(load().rsa_profile(h, 1 if enable else 0))
+
+
+def rsa_kernel_name(kind: int) -> str:
+    return load().rsa_kernel_name(kind).decode()
+
+
+def rsa_kernel_stats(h):
+    """{kernel name: (total ms, launches)} since the previous call."""
+    n = 0
+    while rsa_kernel_name(n):
+        n += 1
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.uint64)
+    _check(load().rsa_kernel_stats(h, ms.ctypes.data, cnt.ctypes.data, n))
+    return {rsa_kernel_name(i): (float(ms[i]), int(cnt[i])) for i in range(n)}
 
 
 def rsa_destroy(h):

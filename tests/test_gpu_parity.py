@@ -45,6 +45,13 @@ def test_small_and_ragged_shapes(L, k):
     _check(L, k, list(range(1, 13)), configs=3)
 
 
+@pytest.mark.parametrize("L,k", [(32, 1), (32, 2), (32, 32), (64, 32), (96, 16), (160, 8),
+                                 (224, 4), (288, 32)])
+def test_tiled_shapes(L, k):
+    # L a multiple of 32 and k a power of two <= 32 run the 32 x 32 tile kernels
+    _check(L, k, list(range(1, 9)), configs=2)
+
+
 @pytest.mark.parametrize("L,k", [(256, 64), (300, 17), (512, 2), (777, 100), (1024, 1)])
 def test_medium_shapes(L, k):
     _check(L, k, list(range(11, 15)), configs=1)
