@@ -37,42 +37,6 @@ __device__ __forceinline__ u64 kmask() {
   return K >= 64 ? ~0ull : ((1ull << K) - 1ull);
 }
 
-// Occupy the k cells of an accepted candidate in the bit lattice, record
-// its node.
-__device__ __forceinline__ void accept_bits(const Group& g, u32* occw, u32 T, u32 s, u32 idx,
-                                            u64 key) {
-  SampleState& st = g.st[s];
-  const u32 node = atomicAdd(&st.n_nodes, 1u);
-  if (node >= g.cap_nodes) { atomicOr(&st.status, ST_NODE_OVF); return; }
-  g.node_key[(size_t)s * g.cap_nodes + node] = key;
-  g.node_idx[(size_t)s * g.cap_nodes + node] = idx;
-  const u32 L = g.L, k = g.k;
-  const u32 o = idx / (u32)g.LL, r = idx % (u32)g.LL;
-  const u32 y0 = r / L, x0 = r % L;
-  g.node_pos[(size_t)s * g.cap_nodes + node] = (o << 31) | (y0 << 15) | x0;
-  u32* ow = occw + (size_t)s * L * T;
-  u32* own = g.owner + (size_t)s * g.LL;
-  if (o == 0) {
-    const u32 b = x0 & 31u, w = x0 >> 5;
-    const u64 m = (k >= 64 ? ~0ull : ((1ull << k) - 1ull)) << b;
-    atomicOr(ow + (size_t)y0 * T + w, (u32)m);
-    if (m >> 32) atomicOr(ow + (size_t)y0 * T + (w + 1 == T ? 0 : w + 1), (u32)(m >> 32));
-    u32 x = x0;
-    for (u32 i = 0; i < k; ++i) {
-      own[(size_t)y0 * L + x] = node;
-      if (++x == L) x = 0;
-    }
-  } else {
-    const u32 bit = 1u << (x0 & 31u), w = x0 >> 5;
-    u32 y = y0;
-    for (u32 i = 0; i < k; ++i) {
-      atomicOr(ow + (size_t)y * T + w, bit);
-      own[(size_t)y * L + x0] = node;
-      if (++y == L) y = 0;
-    }
-  }
-}
-
 // Backward window along one line held in shared memory, one thread:
 //   ln[32 + x] := min(ln[32 + x - K + 1 .. 32 + x])   for x in [0, 32),
 // the line holding positions -32 .. 31 at ln[0 .. 63] (negative positions =
@@ -142,12 +106,71 @@ __device__ __forceinline__ void line_fwd(u64* ln) {
   }
 }
 
-__device__ __forceinline__ u64 key_of(const Group& g, u64 base, u64 idx) {
-  if (g.keys) return g.keys[idx];
-  return mix64(base + SM_GAMMA * (idx + 1));
+constexpr int LN = 65;  // padded line length (u64) of the tile line buffers
+
+// Asynchronous global -> shared copies (cp.async): a tile's staging loads are
+// all in flight together instead of one latency per loop iteration.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-constexpr int LN = 65;  // padded line length (u64) of the tile line buffers
+__device__ __forceinline__ u32 wrap_lo(int v, u32 L) {  // v in [-L, 2L) -> [0, L)
+  return (u32)(v < 0 ? v + (int)L : (v >= (int)L ? v - (int)L : v));
+}
+
+// Persistent loop over (sample, tile) items without 64-bit division.
+struct ItemIter {
+  u32 s, t;
+  __device__ __forceinline__ ItemIter(u32 start, u32 T2) : s(start / T2), t(start % T2) {}
+  __device__ __forceinline__ void next(u32 step, u32 T2) {
+    t += step;
+    while (t >= T2) { t -= T2; ++s; }
+  }
+};
+
+// Accept one candidate with the whole warp (k <= 32): lane i writes cell i.
+// idx and key are warp-uniform.
+__device__ __forceinline__ void accept_warp(const Group& g, u32* occw, u32 T, u32 s, u32 idx,
+                                            u64 key) {
+  const u32 lane = threadIdx.x & 31;
+  SampleState& st = g.st[s];
+  u32 node = 0;
+  if (lane == 0) node = atomicAdd(&st.n_nodes, 1u);
+  node = __shfl_sync(FULL, node, 0);
+  if (node >= g.cap_nodes) {
+    if (lane == 0) atomicOr(&st.status, ST_NODE_OVF);
+    return;
+  }
+  const u32 L = g.L, k = g.k;
+  const u32 o = idx / (u32)g.LL, r = idx - o * (u32)g.LL;
+  const u32 y0 = r / L, x0 = r - y0 * L;
+  if (lane == 0) {
+    g.node_key[(size_t)s * g.cap_nodes + node] = key;
+    g.node_idx[(size_t)s * g.cap_nodes + node] = idx;
+    g.node_pos[(size_t)s * g.cap_nodes + node] = (o << 31) | (y0 << 15) | x0;
+  }
+  u32* ow = occw + (size_t)s * L * T;
+  u32* own = g.owner + (size_t)s * g.LL;
+  if (o == 0) {
+    const u32 b = x0 & 31u, w = x0 >> 5;
+    const u64 m = (k >= 64 ? ~0ull : ((1ull << k) - 1ull)) << b;
+    if (lane == 0) atomicOr(ow + (size_t)y0 * T + w, (u32)m);
+    if (lane == 1 && (m >> 32)) atomicOr(ow + (size_t)y0 * T + (w + 1 == T ? 0 : w + 1), (u32)(m >> 32));
+    if (lane < k) own[(size_t)y0 * L + wrap_lo((int)(x0 + lane), L)] = node;
+  } else if (lane < k) {
+    const u32 y = wrap_lo((int)(y0 + lane), L);
+    atomicOr(ow + (size_t)y * T + (x0 >> 5), 1u << (x0 & 31u));
+    own[(size_t)y * L + x0] = node;
+  }
+}
 
 // Pass 1 of a round.  64 threads per tile, persistent over (sample, tile).
 //  (a) lane-parallel: live priorities of the horizontal candidates anchored
@@ -161,68 +184,181 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
   __shared__ u64 lh[32][LN];    // row lines, positions -32 .. 31
   __shared__ u64 lv[32][LN];    // column lines, positions -32 .. 31
   const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u32 L = g.L, T = tc.T;
-  for (u64 item = blockIdx.x; item < tc.items; item += gridDim.x) {
-    const u32 s = (u32)(item / tc.T2), t = (u32)(item % tc.T2);
+  const u32 L = g.L, T = tc.T, T2 = tc.T2;
+  for (ItemIter it(blockIdx.x, T2); it.s < g.n; it.next(gridDim.x, T2)) {
+    const u32 s = it.s, t = it.t;
     if (g.st[s].done) continue;
-    u8* dflag = dead + (size_t)s * tc.T2 + t;
+    u8* dflag = dead + (size_t)s * T2 + t;
     if (*dflag) continue;
-    const u32 ty = t / T, tx = t % T, Y = ty * 32, X = tx * 32;
+    const u32 ty = t / T, tx = t - ty * T, Y = ty * 32, X = tx * 32;
     const u32* owg = occw + (size_t)s * L * T;
     for (u32 i = threadIdx.x; i < 96 * 3; i += blockDim.x) {
-      const u32 r = i / 3, c = i % 3;
-      ow[r][c] = owg[(size_t)((Y + L + r - 32) % L) * T + (tx + T + c - 1) % T];
+      const u32 r = i / 3, c = i - r * 3;
+      const u32 row = wrap_lo((int)(Y + r) - 32, L);
+      const u32 wc = wrap_lo((int)(tx + c) - 1, T);
+      cp_async4(&ow[r][c], owg + (size_t)row * T + wc);
     }
+    cp_async_wait_all();
     __syncthreads();
-    const u64 base = g.base[s];
-    const bool need_prev = lane >= 33u - K;  // position lane-32 >= -(K-1)
-    if (warp == 0) {
-      // horizontal: lane = position along the row
+    // splitmix64 input of candidate idx is zb + gamma * idx
+    const u64 zb = g.base[s] + SM_GAMMA;
+    const bool caller = g.keys != nullptr;
+    u64 (*ln)[LN] = warp == 0 ? lh : lv;
+    u32 live = 0;          // bit r: line r has a live candidate (warp-uniform)
+    if (K >= 16) {
+      // long windows: the K-1 positions before the tile are hashed in the
+      // same pass as the tile's own, lane = position (slot lane = position
+      // lane - 32, slot 32 + lane = position lane)
+      const bool need_prev = lane >= 33u - K;
+      if (warp == 0) {
+        const u64 zstep = SM_GAMMA * (u64)L;
+        u64 zc = zb + SM_GAMMA * ((u64)Y * L + X + lane);
+        u64 zp = zb + SM_GAMMA * ((u64)Y * L + wrap_lo((int)(X + lane) - 32, L));
 #pragma unroll 2
-      for (u32 r = 0; r < 32; ++r) {
-        const u64 A = ((u64)ow[32 + r][1] << 32) | ow[32 + r][0];  // positions -32 .. 31
-        const u64 B = ((u64)ow[32 + r][2] << 32) | ow[32 + r][1];  // positions 0 .. 63
-        const u64 rowbase = (u64)(Y + r) * L;
-        u64 vp = KEY_NONE, vc = KEY_NONE;
-        if (need_prev && ((A >> lane) & kmask<K>()) == 0)
-          vp = key_of(g, base, rowbase + (X + L - 32 + lane) % L);
-        if (((B >> lane) & kmask<K>()) == 0) vc = key_of(g, base, rowbase + X + lane);
-        lh[r][lane] = vp;
-        lh[r][32 + lane] = vc;
+        for (u32 r = 0; r < 32; ++r, zc += zstep, zp += zstep) {
+          const u64 A = ((u64)ow[32 + r][1] << 32) | ow[32 + r][0];  // positions -32 .. 31
+          const u64 B = ((u64)ow[32 + r][2] << 32) | ow[32 + r][1];  // positions 0 .. 63
+          const bool ap = need_prev && ((A >> lane) & kmask<K>()) == 0;
+          const bool ac = ((B >> lane) & kmask<K>()) == 0;
+          u64 vp = KEY_NONE, vc = KEY_NONE;
+          if (__any_sync(FULL, ap || ac)) {
+            u64 hp, hc;
+            if (caller) {
+              hp = g.keys[(u64)(Y + r) * L + wrap_lo((int)(X + lane) - 32, L)];
+              hc = g.keys[(u64)(Y + r) * L + X + lane];
+            } else {
+              hp = mix64(zp);
+              hc = mix64(zc);
+            }
+            vp = ap ? hp : KEY_NONE;
+            vc = ac ? hc : KEY_NONE;
+            live |= 1u << r;
+          }
+          lh[r][lane] = vp;
+          lh[r][32 + lane] = vc;
+        }
+      } else {
+        const u32 bp = ow[lane][1], bc = ow[32 + lane][1], bn = ow[64 + lane][1];
+        const u64 rowp = g.LL + (u64)wrap_lo((int)(Y + lane) - 32, L) * L + X;
+        const u64 rowc = g.LL + (u64)(Y + lane) * L + X;
+        u64 zc = zb + SM_GAMMA * rowc, zp = zb + SM_GAMMA * rowp;
+#pragma unroll 2
+        for (u32 c = 0; c < 32; ++c, zc += SM_GAMMA, zp += SM_GAMMA) {
+          const u32 Mp = __ballot_sync(FULL, (bp >> c) & 1u);
+          const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
+          const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
+          const u64 A = ((u64)Mc << 32) | Mp, B = ((u64)Mn << 32) | Mc;
+          const bool ap = need_prev && ((A >> lane) & kmask<K>()) == 0;
+          const bool ac = ((B >> lane) & kmask<K>()) == 0;
+          u64 vp = KEY_NONE, vc = KEY_NONE;
+          if (__any_sync(FULL, ap || ac)) {
+            u64 hp, hc;
+            if (caller) {
+              hp = g.keys[rowp + c];
+              hc = g.keys[rowc + c];
+            } else {
+              hp = mix64(zp);
+              hc = mix64(zc);
+            }
+            vp = ap ? hp : KEY_NONE;
+            vc = ac ? hc : KEY_NONE;
+            live |= 1u << c;
+          }
+          lv[c][lane] = vp;
+          lv[c][32 + lane] = vc;
+        }
       }
     } else {
-      // vertical: lane = position along the column
-      const u32 bp = ow[lane][1], bc = ow[32 + lane][1], bn = ow[64 + lane][1];
+      u32 cp = 0, cc = 0;    // vertical warp: occupancy of column `lane`, rows Y-32.. / Y..
+      if (warp == 0) {
+        // tile part of each row, lane = position along the row
+        u64 z = zb + SM_GAMMA * ((u64)Y * L + X + lane);
+        const u64 zstep = SM_GAMMA * (u64)L;
 #pragma unroll 2
-      for (u32 c = 0; c < 32; ++c) {
-        const u32 Mp = __ballot_sync(FULL, (bp >> c) & 1u);
-        const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
-        const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
-        const u64 A = ((u64)Mc << 32) | Mp, B = ((u64)Mn << 32) | Mc;
-        const u64 x = X + c;
-        u64 vp = KEY_NONE, vc = KEY_NONE;
-        if (need_prev && ((A >> lane) & kmask<K>()) == 0)
-          vp = key_of(g, base, g.LL + (u64)((Y + L - 32 + lane) % L) * L + x);
-        if (((B >> lane) & kmask<K>()) == 0) vc = key_of(g, base, g.LL + (u64)(Y + lane) * L + x);
-        lv[c][lane] = vp;
-        lv[c][32 + lane] = vc;
+        for (u32 r = 0; r < 32; ++r, z += zstep) {
+          const u64 B = ((u64)ow[32 + r][2] << 32) | ow[32 + r][1];  // positions 0 .. 63
+          const bool ac = ((B >> lane) & kmask<K>()) == 0;
+          const u32 m = __ballot_sync(FULL, ac);
+          u64 vc = KEY_NONE;
+          if (m) {
+            const u64 h = caller ? g.keys[(u64)(Y + r) * L + X + lane] : mix64(z);
+            vc = ac ? h : KEY_NONE;
+            live |= 1u << r;
+          }
+          lh[r][32 + lane] = vc;
+        }
+      } else {
+        // tile part of each column, lane = position along the column
+        const u32 bp = ow[lane][1], bc = ow[32 + lane][1], bn = ow[64 + lane][1];
+        u64 z = zb + SM_GAMMA * (g.LL + (u64)(Y + lane) * L + X);
+#pragma unroll 2
+        for (u32 c = 0; c < 32; ++c, z += SM_GAMMA) {
+          const u32 Mp = __ballot_sync(FULL, (bp >> c) & 1u);
+          const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
+          const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
+          if (lane == c) { cp = Mp; cc = Mc; }
+          const u64 B = ((u64)Mn << 32) | Mc;
+          const bool ac = ((B >> lane) & kmask<K>()) == 0;
+          const u32 m = __ballot_sync(FULL, ac);
+          u64 vc = KEY_NONE;
+          if (m) {
+            const u64 h = caller ? g.keys[g.LL + (u64)(Y + lane) * L + X + c] : mix64(z);
+            vc = ac ? h : KEY_NONE;
+            live |= 1u << c;
+          }
+          lv[c][32 + lane] = vc;
+        }
+      }
+      // short windows: the K-1 positions before the tile on every line,
+      // packed densely over lanes: item f = i*32 + lane is line f / (K-1),
+      // position -(K-1) + f % (K-1)
+      constexpr u32 KP = K > 1 ? K - 1 : 1;
+#pragma unroll 1
+      for (u32 i = 0; i + 1 < (u32)K; ++i) {
+        const u32 f = i * 32 + lane, line = f / KP, j = f - line * KP;
+        const int pos = (int)j - (int)KP;
+        u64 A;
+        if (warp == 0) {
+          A = ((u64)ow[32 + line][1] << 32) | ow[32 + line][0];  // positions -32 .. 31
+        } else {
+          const u32 lp = __shfl_sync(FULL, cp, line), lc = __shfl_sync(FULL, cc, line);
+          A = ((u64)lc << 32) | lp;
+        }
+        const bool ap = ((A >> (pos + 32)) & kmask<K>()) == 0;
+        const u64 idx = warp == 0 ? (u64)(Y + line) * L + wrap_lo((int)X + pos, L)
+                                  : g.LL + (u64)wrap_lo((int)Y + pos, L) * L + X + line;
+        u64 v = KEY_NONE;
+        if (__any_sync(FULL, ap)) {
+          const u64 h = caller ? g.keys[idx] : mix64(zb + SM_GAMMA * idx);
+          v = ap ? h : KEY_NONE;
+        }
+        ln[line][32 + pos] = v;
+        live |= __reduce_or_sync(FULL, ap ? 1u << line : 0u);
       }
     }
     __syncthreads();
-    if (warp == 0) line_bwd<K>(lh[lane]);
-    else line_bwd<K>(lv[lane]);
+    {
+      u64* mine_ln = ln[lane];
+      if ((live >> lane) & 1u) {
+        line_bwd<K>(mine_ln);
+      } else {
+#pragma unroll 8
+        for (int x = 0; x < 32; ++x) mine_ln[32 + x] = KEY_NONE;
+      }
+    }
     __syncthreads();
     bool any = false;
     u64* cmg = g.cmin + (size_t)s * g.LL;
+#pragma unroll 4
     for (u32 i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
       const u32 y = i >> 5, c = i & 31;
       const u64 v = tmin(lh[y][32 + c], lv[c][32 + y]);
       cmg[(size_t)(Y + y) * L + X + c] = v;
       any |= v != KEY_NONE;
     }
-    const bool live = __syncthreads_or(any);
+    const bool tile_live = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-      if (!live) *dflag = 1;
+      if (!tile_live) *dflag = 1;
       else if (!g.st[s].alive) g.st[s].alive = 1;
     }
   }
@@ -233,7 +369,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
 //      lines (own tile + the tile below); a dead neighbour reads as "none";
 //  (b) one thread per line: width-K forward window minima, in place;
 //  (c) lane-parallel: a live candidate whose window minimum equals its key
-//      is accepted.
+//      is accepted; accepted candidates are written by the whole warp.
 template <int K>
 __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* occw,
                                                     const u8* dead) {
@@ -241,53 +377,78 @@ __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* oc
   __shared__ u64 lh[32][LN];    // row lines: columns X .. X+63
   __shared__ u64 lv[32][LN];    // column lines: rows Y .. Y+63
   const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u32 L = g.L, T = tc.T;
-  for (u64 item = blockIdx.x; item < tc.items; item += gridDim.x) {
-    const u32 s = (u32)(item / tc.T2), t = (u32)(item % tc.T2);
+  const u32 L = g.L, T = tc.T, T2 = tc.T2;
+  for (ItemIter it(blockIdx.x, T2); it.s < g.n; it.next(gridDim.x, T2)) {
+    const u32 s = it.s, t = it.t;
     if (g.st[s].done) continue;
-    const u8* dflag = dead + (size_t)s * tc.T2;
+    const u8* dflag = dead + (size_t)s * T2;
     if (dflag[t]) continue;
-    const u32 ty = t / T, tx = t % T, Y = ty * 32, X = tx * 32;
+    const u32 ty = t / T, tx = t - ty * T, Y = ty * 32, X = tx * 32;
     const u32 txr = tx + 1 == T ? 0 : tx + 1, tyb = ty + 1 == T ? 0 : ty + 1;
     const bool dr = dflag[ty * T + txr] != 0, db = dflag[tyb * T + tx] != 0;
     const u64* cmg = g.cmin + (size_t)s * g.LL;
     const u32* owg = occw + (size_t)s * L * T;
     for (u32 i = threadIdx.x; i < 64 * 2; i += blockDim.x) {
       const u32 r = i >> 1, c = i & 1;
-      ow[r][c] = owg[(size_t)((Y + r) % L) * T + (c ? txr : tx)];
+      cp_async4(&ow[r][c], owg + (size_t)wrap_lo((int)(Y + r), L) * T + (c ? txr : tx));
     }
+#pragma unroll 4
     for (u32 i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
       const u32 r = i >> 5, c = i & 31;
-      const u64 own = cmg[(size_t)(Y + r) * L + X + c];
-      lh[r][c] = own;
-      lv[c][r] = own;
-      lh[r][32 + c] = dr ? KEY_NONE : cmg[(size_t)(Y + r) * L + txr * 32 + c];
-      lv[c][32 + r] = db ? KEY_NONE : cmg[(size_t)(tyb * 32 + r) * L + X + c];
+      const u64* own = cmg + (size_t)(Y + r) * L + X + c;
+      cp_async8(&lh[r][c], own);
+      cp_async8(&lv[c][r], own);
+      if (dr) lh[r][32 + c] = KEY_NONE;
+      else cp_async8(&lh[r][32 + c], cmg + (size_t)(Y + r) * L + txr * 32 + c);
+      if (db) lv[c][32 + r] = KEY_NONE;
+      else cp_async8(&lv[c][32 + r], cmg + (size_t)(tyb * 32 + r) * L + X + c);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (warp == 0) line_fwd<K>(lh[lane]);
     else line_fwd<K>(lv[lane]);
     __syncthreads();
-    const u64 base = g.base[s];
+    const u64 zb = g.base[s] + SM_GAMMA;
+    const bool caller = g.keys != nullptr;
     if (warp == 0) {
-      for (u32 r = 0; r < 32; ++r) {
+      u64 z = zb + SM_GAMMA * ((u64)Y * L + X + lane);
+      const u64 zstep = SM_GAMMA * (u64)L;
+#pragma unroll 2
+      for (u32 r = 0; r < 32; ++r, z += zstep) {
         const u64 f = lh[r][lane];
         const u64 B = ((u64)ow[r][1] << 32) | ow[r][0];
-        if (f != KEY_NONE && ((B >> lane) & kmask<K>()) == 0) {
+        const bool cand = f != KEY_NONE && ((B >> lane) & kmask<K>()) == 0;
+        if (__any_sync(FULL, cand)) {
           const u64 idx = (u64)(Y + r) * L + X + lane;
-          if (f == key_of(g, base, idx)) accept_bits(g, occw, T, s, (u32)idx, f);
+          const u64 key = caller ? g.keys[idx] : mix64(z);
+          u32 m = __ballot_sync(FULL, cand && f == key);
+          while (m) {
+            const u32 src = __ffs(m) - 1;
+            m &= m - 1;
+            accept_warp(g, occw, T, s, (u32)__shfl_sync(FULL, idx, src), __shfl_sync(FULL, f, src));
+          }
         }
       }
     } else {
       const u32 bc = ow[lane][0], bn = ow[32 + lane][0];
-      for (u32 c = 0; c < 32; ++c) {
+      const u64 rowc = g.LL + (u64)(Y + lane) * L + X;
+      u64 z = zb + SM_GAMMA * rowc;
+#pragma unroll 2
+      for (u32 c = 0; c < 32; ++c, z += SM_GAMMA) {
         const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
         const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
         const u64 B = ((u64)Mn << 32) | Mc;
         const u64 f = lv[c][lane];
-        if (f != KEY_NONE && ((B >> lane) & kmask<K>()) == 0) {
-          const u64 idx = g.LL + (u64)(Y + lane) * L + X + c;
-          if (f == key_of(g, base, idx)) accept_bits(g, occw, T, s, (u32)idx, f);
+        const bool cand = f != KEY_NONE && ((B >> lane) & kmask<K>()) == 0;
+        if (__any_sync(FULL, cand)) {
+          const u64 idx = rowc + c;
+          const u64 key = caller ? g.keys[idx] : mix64(z);
+          u32 m = __ballot_sync(FULL, cand && f == key);
+          while (m) {
+            const u32 src = __ffs(m) - 1;
+            m &= m - 1;
+            accept_warp(g, occw, T, s, (u32)__shfl_sync(FULL, idx, src), __shfl_sync(FULL, f, src));
+          }
         }
       }
     }
