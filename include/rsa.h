@@ -69,6 +69,26 @@ int rsa_run_seeds(rsa_t *h, const uint64_t *seeds, uint32_t n, void *stream);
  * (RSA_EINVAL otherwise). */
 int rsa_run_keys(rsa_t *h, const uint64_t *keys, void *stream);
 
+/* Workspace-free batched run (the paper has no counterpart; this is an
+ * interface for callers that cannot allocate device memory: processes whose
+ * device memory pool belongs to another allocator, or latency-critical loops
+ * that must not call cudaMalloc/cudaFree, which can synchronise the device).
+ * Same computation and results as rsa_run_seeds + rsa_results for the n
+ * samples with the given seeds, but all device state lives in one fixed
+ * 64 MiB array inside the library (held by every GPU that loads it until the
+ * process exits); no handle, no device or pinned allocation.
+ *   seeds: host array of n seeds (read);  n_j, n_c: host arrays of n (written).
+ * Sizes whose workspace (rsa_workspace_bytes(L, k, n)) exceeds 64 MiB are
+ * rejected with RSA_EINVAL.  The first call on a device looks up the array's
+ * device address (once per device, with that device current); make that
+ * first call before any stream capture starts on the device.  Every call
+ * reuses the same array: a call re-initialises what it needs, but two calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it.
+ * Synchronises `stream` like rsa_run_seeds; returns the first per-sample
+ * error code, as rsa_results does. */
+int rsa_run_static(uint32_t L, uint32_t k, const uint64_t *seeds, uint32_t n, uint32_t *n_j,
+                   uint32_t *n_c, void *stream);
+
 /* Copy the last run's results to caller-owned host arrays of length n
  * (n <= samples of the last run; either pointer may be NULL).  Synchronises
  * the run's stream.  Returns the first per-sample error code, if any; a

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -487,6 +489,41 @@ int fetch_states(rsa_t* h, std::vector<SampleState>& out) {
   return 0;
 }
 
+// ---------------------------------------------------------------------
+// Workspace-free runs.  Some callers cannot call cudaMalloc: a process whose
+// device memory pool is owned by another allocator (a framework's caching
+// allocator that has reserved the whole HBM), or a latency-critical serving
+// loop that must not hit the device-wide synchronisation cudaMalloc and
+// cudaFree can cause.  rsa_run_static serves them from this fixed array,
+// which every GPU that loads the library holds until the process exits.
+// ---------------------------------------------------------------------
+constexpr size_t STATIC_WS_BYTES = 64ull << 20;  // 64 MiB
+static __device__ __align__(256) unsigned char g_static_ws[STATIC_WS_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[MAX_DEVICES] = {};
+
+// Device address of g_static_ws on the current device, looked up once per
+// device (with that device current).  In host code the symbol itself is only
+// a host-side stand-in, never a device address.
+int static_workspace(void** out) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= MAX_DEVICES) return fail(RSA_EINVAL, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
+    if (e != cudaSuccess || !p)
+      return fail(RSA_ECUDA, std::string("cudaGetSymbolAddress(static workspace): ") +
+                                 cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -530,6 +567,51 @@ int rsa_run_keys(rsa_t* h, const uint64_t* keys, void* stream) {
   }
   uint64_t seed = h->seed;
   return run_impl(h, &seed, 1, keys, static_cast<cudaStream_t>(stream));
+}
+
+int rsa_run_static(uint32_t L, uint32_t k, const uint64_t* seeds, uint32_t n, uint32_t* n_j,
+                   uint32_t* n_c, void* stream) {
+  if (!seeds || !n_j || !n_c) return fail(RSA_EINVAL, "null seeds or output array");
+  if (!(k >= 1 && k <= L && L <= 32768)) return fail(RSA_EINVAL, "need 1 <= k <= L <= 32768");
+  if (n == 0) return fail(RSA_EINVAL, "n must be >= 1");
+  rsa h;
+  h.L = L;
+  h.k = k;
+  h.seed = 0;
+  h.geo = plan(L, k);
+  const size_t need = layout_of(L, k, n, false, h.geo).total;
+  if (need > STATIC_WS_BYTES)
+    return fail(RSA_EINVAL, "rsa_run_static: L=" + std::to_string(L) + " k=" + std::to_string(k) +
+                                " n=" + std::to_string(n) + " needs " + std::to_string(need) +
+                                " bytes of workspace; the static workspace holds " +
+                                std::to_string(STATIC_WS_BYTES));
+  void* ws = nullptr;
+  int rc = static_workspace(&ws);
+  if (rc) return rc;
+  h.bound_ptr = ws;  // the run's buffers (all re-initialised by the run) live here
+  h.bound_bytes = STATIC_WS_BYTES;
+  u32 counter[4] = {0, 0, 0, 0};  // pageable host word for the loop checks
+  h.h_counter = counter;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = run_impl(&h, seeds, n, nullptr, st);
+  h.h_counter = nullptr;
+  if (rc) return rc;
+  // results straight from the per-sample state records (strided copies)
+  const char* sts = static_cast<const char*>(ws) + h.lay.st;
+  CUDA_TRY(cudaMemcpy2DAsync(n_c, sizeof(u32), sts + offsetof(SampleState, status),
+                             sizeof(SampleState), sizeof(u32), n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  int first = 0;
+  for (u32 i = 0; i < n && !first; ++i) {
+    first = status_code(n_c[i]);
+    if (first) g_err = "sample " + std::to_string(i) + " status bits " + std::to_string(n_c[i]);
+  }
+  CUDA_TRY(cudaMemcpy2DAsync(n_j, sizeof(u32), sts + offsetof(SampleState, n_nodes),
+                             sizeof(SampleState), sizeof(u32), n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpy2DAsync(n_c, sizeof(u32), sts + offsetof(SampleState, nc),
+                             sizeof(SampleState), sizeof(u32), n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  return first;
 }
 
 int rsa_results(rsa_t* h, uint32_t* n_j, uint32_t* n_c, uint32_t n) {

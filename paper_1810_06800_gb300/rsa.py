@@ -19,7 +19,8 @@ RSA_OK, RSA_EINVAL, RSA_ENOMEM, RSA_ECUDA, RSA_ETIMEOUT, RSA_ENOWRAP, RSA_ESTATE
     0, -1, -2, -3, -4, -5, -6)
 _NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_ECUDA",
           RSA_ETIMEOUT: "RSA_ETIMEOUT", RSA_ENOWRAP: "RSA_ENOWRAP", RSA_ESTATE: "RSA_ESTATE"}
-SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_results",
+SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_run_static",
+           "rsa_results",
            "rsa_sample_stats", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
            "rsa_profile", "rsa_kernel_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
@@ -51,6 +52,7 @@ def load():
     lib.rsa_run_batch.argtypes = [vp, u32, vp]
     lib.rsa_run_seeds.argtypes = [vp, vp, u32, vp]
     lib.rsa_run_keys.argtypes = [vp, vp, vp]
+    lib.rsa_run_static.argtypes = [u32, u32, vp, u32, vp, vp, vp]
     lib.rsa_results.argtypes = [vp, vp, vp, u32]
     lib.rsa_sample_stats.argtypes = [vp, vp, vp, vp, vp, u32]
     lib.rsa_accepted.argtypes = [vp, u32, vp, u32, ctypes.POINTER(u32)]
@@ -106,6 +108,18 @@ def rsa_run_seeds(h, seeds, stream=None):
 def rsa_run_keys(h, keys, stream=None):
     a = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
     return _check(load().rsa_run_keys(h, a.ctypes.data, _stream_ptr(stream)))
+
+
+def rsa_run_static(L: int, k: int, seeds, stream=None):
+    """Workspace-free run: no handle, no device allocation (for callers that
+    cannot allocate device memory); same results as rsa_run_seeds +
+    rsa_results.  Returns (n_j, n_c)."""
+    a = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    nj = np.zeros(a.size, dtype=np.uint32)
+    nc = np.zeros(a.size, dtype=np.uint32)
+    _check(load().rsa_run_static(L, k, a.ctypes.data, a.size, nj.ctypes.data, nc.ctypes.data,
+                                 _stream_ptr(stream)))
+    return nj, nc
 
 
 def rsa_results(h, n: int, check: bool = True):
