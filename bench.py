@@ -31,12 +31,31 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "L1024_k32_x1000": dict(L=1024, k=32, n=1000),
     "L64_k4_x100": dict(L=64, k=4, n=100),
+    # small case of the headline shape for ncu captures (a few GB on the device)
+    "L1024_k32_x64": dict(L=1024, k=32, n=64),
 }
 METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
-# algorithmic bytes per lattice cell and per launch of each round kernel
-# (the design doc derives them): cell-min passes read occupancy (1 B) and write or
-# read-modify-write the 8-byte cell minimum; acceptance passes read it.
+# Algorithmic work of the round kernels.  Byte-type kernels (the general
+# line path): bytes per lattice cell per launch -- the cell-minimum passes
+# read occupancy (1 B) and write or read-modify-write the 8-byte cell
+# minimum, the acceptance passes read it.
 BYTES_PER_CELL = {"k_row_cmin": 9, "k_col_cmin": 17, "k_row_accept": 8, "k_col_accept": 8}
+# Integer-ALU kernels (the 32x32 tile path), counted in 32-bit lane
+# operations: a 64-bit minimum is 4 ops (two compares, two selects), a
+# width-k window minimum by van Herk / Gil-Werman is 3 minima per cell, a
+# liveness test of a candidate's k cells is 4 ops (shift, mask, compare of a
+# 64-bit word), a splitmix64 priority is 20 ops (64-bit add 2, three 64-bit
+# xor-shifts at 4, two 64-bit constant multiplies at 3).
+OPS_PER_KEY = 20
+OPS_PER_CELL = {
+    # horizontal and vertical window minima, their combination, two liveness tests
+    "k_tile_cmin": 2 * 3 * 4 + 4 + 2 * 4,
+    # two forward window minima, two liveness tests; plus a compare per key
+    "k_tile_accept": 2 * 3 * 4 + 2 * 4,
+}
+TILE_WORK = {"k_tile_cmin": ("cmin_cells", "cmin_keys"),
+             "k_tile_accept": ("accept_cells", "accept_keys")}
+ALU_LANES_PER_SM = 128  # 4 schedulers x 32 lanes, one integer op per lane per clock
 
 
 def src_digest() -> str:
@@ -213,6 +232,7 @@ def main():
         rsa.rsa_run_seeds(h, seeds, stream)
     torch.cuda.synchronize()
     rsa.rsa_kernel_stats(h)  # reset counters
+    rsa.rsa_work_stats(h)
 
     # ---- device-timed region (inputs resident: seeds + workspace) ----
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
@@ -232,6 +252,7 @@ def main():
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     kstats = rsa.rsa_kernel_stats(h)
+    work = rsa.rsa_work_stats(h)
     rsa.rsa_profile(h, False)
     st = rsa.rsa_sample_stats(h, n)
     nj, nc = rsa.rsa_results(h, n)
@@ -270,25 +291,43 @@ def main():
     dom = max(ours, key=lambda nm: ours[nm][0])
     dom_ms, dom_launches = ours[dom]
     passes = int(np.sum(st["rounds"].astype(np.int64) + 1)) * args.steps
-    peak, peak_kind = measured_peaks()
-    roof = None
-    if dom in BYTES_PER_CELL:
+    hbm_peak, peak_kind = measured_peaks()
+    traffic_db = {}
+    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            traffic_db = json.load(f)
+    ent = traffic_db.get(dom)
+    fresh = bool(ent) and ent.get("src") == src_digest()
+    if dom in TILE_WORK:
+        cells_key, keys_key = TILE_WORK[dom]
+        cells, keys = work[cells_key], work[keys_key]
+        ops = cells * OPS_PER_CELL[dom] + keys * (OPS_PER_KEY + (4 if dom == "k_tile_accept" else 0))
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) \
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
+        peak = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e9  # Gop/s
+        achieved = ops / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "Gop/s", "frac": achieved / peak,
+                "traffic": (ent["bytes_per_cell"] * cells / dom_launches) if fresh else None,
+                "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} int lanes x {sm_mhz:.0f} MHz",
+                "alg_ops_per_launch": ops / dom_launches,
+                "cells_per_launch": cells / dom_launches,
+                "hbm_view": {"alg_bytes_per_launch": 8.0 * cells / dom_launches,
+                             "achieved_gbs": 8.0 * cells / (dom_ms / 1e3) / 1e9,
+                             "peak_gbs": hbm_peak,
+                             "frac": 8.0 * cells / (dom_ms / 1e3) / 1e9 / hbm_peak}}
+    elif dom in BYTES_PER_CELL:
         alg_bytes = BYTES_PER_CELL[dom] * passes * L * L
         achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-        traffic = None
-        tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-        if os.path.exists(tp):
-            with open(tp) as f:
-                tj = json.load(f)
-            ent = tj.get(dom)
-            if ent and ent.get("src") == src_digest():
-                traffic = ent["bytes_per_cell"] * (passes * L * L) / dom_launches
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": (ent["bytes_per_cell"] * passes * L * L / dom_launches) if fresh else None,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "alg_bytes_per_launch": alg_bytes / dom_launches}
     else:
-        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": peak,
+        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": hbm_peak,
                 "unit": "GB/s", "frac": None, "traffic": None}
     kernel_table = {nm: {"ms": round(v[0], 3), "launches": v[1],
                          "share": round(v[0] / sum(x[0] for x in ours.values()), 4)}

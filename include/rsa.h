@@ -115,6 +115,12 @@ int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_
 int rsa_profile(rsa_t *h, int enable);
 int rsa_kernel_stats(rsa_t *h, double *ms, unsigned long long *launches, uint32_t n_kinds);
 const char *rsa_kernel_name(uint32_t kind);
+/* Work done by the tiled round kernels since the previous call (then reset):
+ * out[0] cells of live tiles processed by the cell-minimum pass, out[1]
+ * live candidates it gave a priority, out[2] / out[3] the same for the
+ * acceptance pass (n <= 4 values are written).  Zero for shapes that do not
+ * use the tiled kernels. */
+int rsa_work_stats(rsa_t *h, unsigned long long *out, uint32_t n);
 
 /* Bytes of device workspace a run of n_samples needs for (L, k). */
 int rsa_workspace_bytes(uint32_t L, uint32_t k, uint32_t n_samples, uint64_t *bytes);

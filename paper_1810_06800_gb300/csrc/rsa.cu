@@ -212,7 +212,8 @@ struct rsa {
   u32 last_n = 0;
   bool with_keys = false;
   cudaStream_t stream = nullptr;
-  u32* h_counter = nullptr;  // pinned
+  u32* h_counter = nullptr;  // pinned, 64 bytes: loop counters + work counters
+  unsigned long long work[4] = {0, 0, 0, 0};  // accumulated tile-pass work
   int device = -1;
   int sm_count = 0;
   int tile_blocks[2] = {0, 0};  // resident blocks per SM: cmin, accept
@@ -274,6 +275,7 @@ Group group_of(rsa_t* h, u32 n) {
   g.edges = reinterpret_cast<Edge*>(b + l.edges);
   g.st = reinterpret_cast<SampleState*>(b + l.st);
   g.scratch = reinterpret_cast<u64*>(b + l.scratch);
+  g.work = reinterpret_cast<u64*>(b + l.counters + 16);
   return g;
 }
 
@@ -371,7 +373,7 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   if (n == 0) return fail(RSA_EINVAL, "n_samples must be >= 1");
   int rc;
   CUDA_TRY(cudaGetDevice(&h->device));
-  if (!h->h_counter) CUDA_TRY(cudaMallocHost(&h->h_counter, 16));
+  if (!h->h_counter) CUDA_TRY(cudaMallocHost(&h->h_counter, 64));
   h->with_keys = keys != nullptr;
   if ((rc = ensure_workspace(h, n, h->with_keys))) return rc;
   h->stream = stream;
@@ -394,6 +396,7 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
     CUDA_TRY(cudaMemsetAsync(g.occ, 0, (size_t)n * LL, stream));
   }
   CUDA_TRY(cudaMemsetAsync(g.owner, 0xFF, (size_t)n * LL * 4, stream));
+  CUDA_TRY(cudaMemsetAsync(b + l.counters, 0, 64, stream));
   launch(h, KD_INIT, k_init, dim3((n + 127) / 128), dim3(128), 0, stream, g,
          (const u64*)d_seeds);
   if ((rc = launch_check("k_init"))) return rc;
@@ -468,6 +471,12 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
       if (open == 0) break;
     }
   }
+  // tile-pass work counters of this run (for throughput accounting)
+  CUDA_TRY(cudaMemcpyAsync(h->h_counter + 4, b + l.counters + 16, 32, cudaMemcpyDeviceToHost,
+                           stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  const unsigned long long* wk = reinterpret_cast<const unsigned long long*>(h->h_counter + 4);
+  for (int i = 0; i < 4; ++i) h->work[i] += wk[i];
   return 0;
 }
 
@@ -590,7 +599,7 @@ int rsa_run_static(uint32_t L, uint32_t k, const uint64_t* seeds, uint32_t n, ui
   if (rc) return rc;
   h.bound_ptr = ws;  // the run's buffers (all re-initialised by the run) live here
   h.bound_bytes = STATIC_WS_BYTES;
-  u32 counter[4] = {0, 0, 0, 0};  // pageable host word for the loop checks
+  alignas(8) u32 counter[16] = {};  // pageable host words for the loop checks
   h.h_counter = counter;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = run_impl(&h, seeds, n, nullptr, st);
@@ -708,6 +717,15 @@ int rsa_kernel_stats(rsa_t* h, double* ms, unsigned long long* launches, uint32_
     if (launches) launches[i] = p.launches[i];
     p.ms[i] = 0.0;
     p.launches[i] = 0;
+  }
+  return 0;
+}
+
+int rsa_work_stats(rsa_t* h, unsigned long long* out, uint32_t n) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  for (uint32_t i = 0; i < n && i < 4; ++i) {
+    if (out) out[i] = h->work[i];
+    h->work[i] = 0;
   }
   return 0;
 }

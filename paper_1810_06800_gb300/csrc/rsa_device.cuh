@@ -87,6 +87,8 @@ struct Group {         // one batch of samples sharing (L, k)
   u32* nbkt;           // [n][NBKT + 1] bucket offsets into nkey_b
   SampleState* st;     // [n]
   u64* scratch;        // global scratch for very long windows (or null)
+  u64* work;           // [4] work counters of the tile passes: cmin cells,
+                       //     cmin keys, accept cells, accept keys
 };
 
 __device__ __forceinline__ u64 cand_key(const Group& g, u32 s, u64 idx) {

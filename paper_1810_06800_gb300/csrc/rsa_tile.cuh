@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
     const bool caller = g.keys != nullptr;
     u64 (*ln)[LN] = warp == 0 ? lh : lv;
     u32 live = 0;          // bit r: line r has a live candidate (warp-uniform)
+    u32 keyed = 0;         // live candidates given a key (warp-uniform)
     if (K >= 16) {
       // long windows: the K-1 positions before the tile are hashed in the
       // same pass as the tile's own, lane = position (slot lane = position
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             vp = ap ? hp : KEY_NONE;
             vc = ac ? hc : KEY_NONE;
             live |= 1u << r;
+            keyed += __popc(__ballot_sync(FULL, ap)) + __popc(__ballot_sync(FULL, ac));
           }
           lh[r][lane] = vp;
           lh[r][32 + lane] = vc;
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             vp = ap ? hp : KEY_NONE;
             vc = ac ? hc : KEY_NONE;
             live |= 1u << c;
+            keyed += __popc(__ballot_sync(FULL, ap)) + __popc(__ballot_sync(FULL, ac));
           }
           lv[c][lane] = vp;
           lv[c][32 + lane] = vc;
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             const u64 h = caller ? g.keys[(u64)(Y + r) * L + X + lane] : mix64(z);
             vc = ac ? h : KEY_NONE;
             live |= 1u << r;
+            keyed += __popc(m);
           }
           lh[r][32 + lane] = vc;
         }
@@ -305,6 +309,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             const u64 h = caller ? g.keys[g.LL + (u64)(Y + lane) * L + X + c] : mix64(z);
             vc = ac ? h : KEY_NONE;
             live |= 1u << c;
+            keyed += __popc(m);
           }
           lv[c][32 + lane] = vc;
         }
@@ -334,6 +339,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
         }
         ln[line][32 + pos] = v;
         live |= __reduce_or_sync(FULL, ap ? 1u << line : 0u);
+        keyed += __popc(__ballot_sync(FULL, ap));
       }
     }
     __syncthreads();
@@ -357,7 +363,9 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
       any |= v != KEY_NONE;
     }
     const bool tile_live = __syncthreads_or(any);
+    if (lane == 0 && keyed) atomicAdd(g.work + 1, (u64)keyed);
     if (threadIdx.x == 0) {
+      atomicAdd(g.work + 0, 1024ull);
       if (!tile_live) *dflag = 1;
       else if (!g.st[s].alive) g.st[s].alive = 1;
     }
@@ -410,6 +418,7 @@ __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* oc
     __syncthreads();
     const u64 zb = g.base[s] + SM_GAMMA;
     const bool caller = g.keys != nullptr;
+    u32 keyed = 0;
     if (warp == 0) {
       u64 z = zb + SM_GAMMA * ((u64)Y * L + X + lane);
       const u64 zstep = SM_GAMMA * (u64)L;
@@ -421,6 +430,7 @@ __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* oc
         if (__any_sync(FULL, cand)) {
           const u64 idx = (u64)(Y + r) * L + X + lane;
           const u64 key = caller ? g.keys[idx] : mix64(z);
+          keyed += __popc(__ballot_sync(FULL, cand));
           u32 m = __ballot_sync(FULL, cand && f == key);
           while (m) {
             const u32 src = __ffs(m) - 1;
@@ -443,6 +453,7 @@ __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* oc
         if (__any_sync(FULL, cand)) {
           const u64 idx = rowc + c;
           const u64 key = caller ? g.keys[idx] : mix64(z);
+          keyed += __popc(__ballot_sync(FULL, cand));
           u32 m = __ballot_sync(FULL, cand && f == key);
           while (m) {
             const u32 src = __ffs(m) - 1;
@@ -452,6 +463,8 @@ __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* oc
         }
       }
     }
+    if (lane == 0 && keyed) atomicAdd(g.work + 3, (u64)keyed);
+    if (threadIdx.x == 0) atomicAdd(g.work + 2, 1024ull);
     __syncthreads();
   }
 }

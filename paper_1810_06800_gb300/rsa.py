@@ -22,7 +22,7 @@ _NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_EC
 SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_run_static",
            "rsa_results",
            "rsa_sample_stats", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
-           "rsa_profile", "rsa_kernel_stats", "rsa_destroy", "rsa_kernel_name",
+           "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
 _lib = None
@@ -62,6 +62,7 @@ def load():
     lib.rsa_destroy.restype = None
     lib.rsa_profile.argtypes = [vp, ip]
     lib.rsa_kernel_stats.argtypes = [vp, vp, vp, u32]
+    lib.rsa_work_stats.argtypes = [vp, vp, u32]
     lib.rsa_kernel_name.argtypes = [u32]
     lib.rsa_kernel_name.restype = ctypes.c_char_p
     lib.rsa_last_error.argtypes = []
@@ -183,6 +184,14 @@ def rsa_kernel_stats(h):
     cnt = np.zeros(n, dtype=np.uint64)
     _check(load().rsa_kernel_stats(h, ms.ctypes.data, cnt.ctypes.data, n))
     return {rsa_kernel_name(i): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+
+def rsa_work_stats(h):
+    """Tile-pass work since the previous call: dict of cell and key counts."""
+    out = np.zeros(4, dtype=np.uint64)
+    _check(load().rsa_work_stats(h, out.ctypes.data, 4))
+    return dict(cmin_cells=int(out[0]), cmin_keys=int(out[1]), accept_cells=int(out[2]),
+                accept_keys=int(out[3]))
 
 
 def rsa_destroy(h):
