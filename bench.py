@@ -139,6 +139,23 @@ def dist_setup():
     return world, rank, local
 
 
+def shard_seeds(rank: int, n: int):
+    """Seeds of rank r: r*n + 1 .. r*n + n (weak scaling, disjoint across ranks)."""
+    import numpy as np
+    return np.arange(rank * n + 1, rank * n + n + 1, dtype=np.uint64)
+
+
+def max_over_ranks(value: float, pg, device=None) -> float:
+    """Slowest rank's time; `pg` is torch.distributed (or None for one rank)."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_rate(L, k, seeds, budget_s, threads):
     """Samples/s of the oracle on `threads` host threads over a bounded
     prefix of the seeds (grown until it takes at least budget_s)."""
@@ -218,7 +235,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     L, k, n = wl["L"], wl["k"], wl["n"]
-    seeds = np.arange(rank * n + 1, rank * n + n + 1, dtype=np.uint64)
+    seeds = shard_seeds(rank, n)
     stream = torch.cuda.current_stream()
     lat = rsa.Lattice(L, k)
     h = lat.h
@@ -256,10 +273,7 @@ def main():
     rsa.rsa_profile(h, False)
     st = rsa.rsa_sample_stats(h, n)
     nj, nc = rsa.rsa_results(h, n)
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, pg, "cuda")
     value = n * world * args.steps / (ms / 1e3)
 
     # ---- end-to-end through the C ABI with host buffers ----
@@ -273,10 +287,7 @@ def main():
         nj_h, nc_h = rsa.rsa_results(h, n)     # device -> host results
     barrier()
     wall = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([wall], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        wall = float(t.item())
+    wall = max_over_ranks(wall, pg, "cuda")
     e2e = n * world * args.steps / wall
     assert np.array_equal(nj_h, nj) and np.array_equal(nc_h, nc)
 
