@@ -19,6 +19,7 @@
 #include "../../include/rsa.h"
 #include "rsa_kernels.cuh"
 #include "rsa_tile.cuh"
+#include "rsa_line.cuh"
 
 using namespace rsak;
 
@@ -47,13 +48,16 @@ constexpr size_t SMEM_BUDGET = 160 * 1024;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t occ, occw, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
+  size_t occ, occw, occT, cB, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
       ebkt, nkey_b, nbkt, st, seeds, counters, keys,
       scratch, total;
 };
 
 struct Geometry {
   bool tile;                    // power-of-two k <= 32 and L % 32 == 0
+  bool line;                    // 32 <= k <= LINE_KMAX, L % 32 == 0, not tile
+  LineCfg lc;
+  size_t line_smem;
   TileCfg tc;                   // (items filled per run)
   RowCfg row;
   ColCfg col;
@@ -77,6 +81,18 @@ Geometry plan(u32 L, u32 k) {
   G.tile = tile_shape(L, k);
   G.tc.T = L / 32;
   G.tc.T2 = G.tc.T * G.tc.T;
+  G.line = !G.tile && L % 32 == 0 && k >= 32 && k <= LINE_KMAX;
+  if (G.line) {
+    // longest segment (multiple of 32, <= 4096) whose buffers stay near 100 KB,
+    // so at least two blocks fit on an SM
+    u32 S = std::min<u32>(L, 4096);
+    while (S > 256 && line_smem_bytes(S + k - 1, S, k) > 100 * 1024) S -= 256;
+    G.lc.S = S;
+    G.lc.nseg = (L + S - 1) / S;
+    G.lc.nmax = S + k - 1;
+    G.lc.T = L / 32;
+    G.line_smem = line_smem_bytes(G.lc.nmax, S, k);
+  }
   // ---- row pass: one warp per (row, segment) ----
   RowCfg& r = G.row;
   r.S = L <= 4096 ? L : 4096;
@@ -143,8 +159,11 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
     off = align_up(off + bytes);
     return at;
   };
-  l.occ = take(G.tile ? 0 : n * LL);
-  l.occw = take(G.tile ? n * LL / 8 : 0);
+  const bool bits = G.tile || G.line;
+  l.occ = take(bits ? 0 : n * LL);
+  l.occw = take(bits ? n * LL / 8 : 0);
+  l.occT = take(G.line ? n * LL / 8 : 0);
+  l.cB = take(G.line ? n * LL * 8 : 0);
   l.dead = take(G.tile ? (size_t)n * G.tc.T2 : 0);
   l.owner = take(n * LL * 4);
   l.cmin = take(n * LL * 8);
@@ -163,7 +182,7 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   l.counters = take(64);
   l.keys = take(with_keys ? 2 * LL * 8 : 0);
   // scratch blocks are indexed by (sample, block) in the kernels
-  l.scratch = take(G.tile ? 0 : G.scratch_words * 8 * n);
+  l.scratch = take(bits ? 0 : G.scratch_words * 8 * n);
   l.total = off;
   return l;
 }
@@ -179,11 +198,13 @@ int set_smem(F* fn, size_t bytes) {
 
 enum Kind {
   KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
+  KD_LINE_CMIN_H, KD_LINE_CMIN_V, KD_LINE_COMBINE, KD_LINE_ACCEPT_H, KD_LINE_ACCEPT_V,
   KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE, KD_COUNT
 };
 const char* const kKindNames[KD_COUNT] = {
     "k_init",         "k_row_cmin",    "k_col_cmin",   "k_row_accept", "k_col_accept",
-    "k_tile_cmin",    "k_tile_accept", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
+    "k_tile_cmin",    "k_tile_accept", "k_line_cmin_h", "k_line_cmin_v", "k_line_combine",
+    "k_line_accept_h", "k_line_accept_v", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
     "k_probe_copy",   "k_probe",       "k_search_decide"};
 
 // Optional per-kernel timing with CUDA events recorded around each launch
@@ -392,6 +413,9 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   if (G.tile) {
     CUDA_TRY(cudaMemsetAsync(b + l.occw, 0, (size_t)n * LL / 8, stream));
     CUDA_TRY(cudaMemsetAsync(b + l.dead, 0, (size_t)n * G.tc.T2, stream));
+  } else if (G.line) {
+    CUDA_TRY(cudaMemsetAsync(b + l.occw, 0, (size_t)n * LL / 8, stream));
+    CUDA_TRY(cudaMemsetAsync(b + l.occT, 0, (size_t)n * LL / 8, stream));
   } else {
     CUDA_TRY(cudaMemsetAsync(g.occ, 0, (size_t)n * LL, stream));
   }
@@ -401,7 +425,12 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
          (const u64*)d_seeds);
   if ((rc = launch_check("k_init"))) return rc;
 
-  if (!G.tile) {
+  if (G.line) {
+    if ((rc = set_smem(k_line_cmin<0>, G.line_smem))) return rc;
+    if ((rc = set_smem(k_line_cmin<1>, G.line_smem))) return rc;
+    if ((rc = set_smem(k_line_accept<0>, G.line_smem))) return rc;
+    if ((rc = set_smem(k_line_accept<1>, G.line_smem))) return rc;
+  } else if (!G.tile) {
     if ((rc = set_smem(k_row<0>, G.row_smem))) return rc;
     if ((rc = set_smem(k_row<1>, G.row_smem))) return rc;
     if ((rc = set_smem(k_col<0>, G.col_smem))) return rc;
@@ -425,6 +454,19 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
     CUDA_TRY(cudaMemsetAsync(d_counter, 0, 4, stream));
     if (G.tile) {
       if ((rc = launch_tile(h, g, tc, occw, dead, tgrid, stream))) return rc;
+    } else if (G.line) {
+      u32* occT = reinterpret_cast<u32*>(b + l.occT);
+      u64* cB = reinterpret_cast<u64*>(b + l.cB);
+      const dim3 lg(h->L * G.lc.nseg, n), tg(G.tc.T2, n);
+      launch(h, KD_LINE_CMIN_H, k_line_cmin<0>, lg, dim3(LINE_THREADS), G.line_smem, stream, g,
+             G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
+      launch(h, KD_LINE_CMIN_V, k_line_cmin<1>, lg, dim3(LINE_THREADS), G.line_smem, stream, g,
+             G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
+      launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, stream, g, g.cmin, cB);
+      launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_smem, stream,
+             g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
+      launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_smem, stream,
+             g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
     } else {
       launch(h, KD_ROW_CMIN, k_row<0>, rg, dim3(G.row_threads), G.row_smem, stream, g, G.row);
       launch(h, KD_COL_CMIN, k_col<0>, cg, dim3(G.col_threads), G.col_smem, stream, g, G.col);

@@ -52,6 +52,13 @@ def test_tiled_shapes(L, k):
     _check(L, k, list(range(1, 9)), configs=2)
 
 
+@pytest.mark.parametrize("L,k", [(64, 33), (96, 48), (128, 100), (160, 96), (320, 320),
+                                 (512, 64), (1024, 128)])
+def test_long_k_line_shapes(L, k):
+    # L a multiple of 32 and 32 < k <= 4096 run the transposed line kernels
+    _check(L, k, list(range(1, 7)), configs=2)
+
+
 @pytest.mark.parametrize("L,k", [(256, 64), (300, 17), (512, 2), (777, 100), (1024, 1)])
 def test_medium_shapes(L, k):
     _check(L, k, list(range(11, 15)), configs=1)
