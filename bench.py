@@ -31,8 +31,9 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "L1024_k32_x1000": dict(L=1024, k=32, n=1000),
     "L64_k4_x100": dict(L=64, k=4, n=100),
-    # small case of the headline shape for ncu captures (a few GB on the device)
+    # small cases for ncu captures (a few GB on the device)
     "L1024_k32_x64": dict(L=1024, k=32, n=64),
+    "L8192_k512_x2": dict(L=8192, k=512, n=2),
 }
 METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
 # Algorithmic work of the round kernels.  Byte-type kernels (the general

@@ -43,16 +43,19 @@ __device__ void block_seg_scan(const u64* src, u64* dst, u32 n, u32 k, u64* wv, 
   const u32 a = min(tid * C, n), b = min(a + C, n);
   u64 run = KEY_NONE;
   bool flag = false;
+  // one division per thread: the first block boundary inside the chunk
   if (FWD) {
+    u32 nb = (a + k - 1) / k * k;        // next block start >= a
     for (u32 u = a; u < b; ++u) {
-      if (u % k == 0) { run = KEY_NONE; flag = true; }
+      if (u == nb) { run = KEY_NONE; flag = true; nb += k; }
       run = tmin(run, src[u]);
       dst[u] = run;
     }
   } else {
+    u32 ne = b / k * k;                  // last block start <= b: p = ne - 1 ends a block
     for (u32 u = b; u > a; --u) {
       const u32 p = u - 1;
-      if ((p + 1) % k == 0) { run = KEY_NONE; flag = true; }
+      if (p + 1 == ne) { run = KEY_NONE; flag = true; ne -= k; }
       run = tmin(run, src[p]);
       dst[p] = run;
     }
@@ -128,9 +131,12 @@ __device__ __forceinline__ u32 bits_before(const u32* w, const u32* wpre, u32 po
 __device__ __forceinline__ void stage_bits(const u32* occ_line, u32 T, int p0, u32 nwords, u32* w,
                                            u32* wpre, u32* scratch) {
   for (u32 i = threadIdx.x; i < nwords; i += blockDim.x) {
+    // p0 / 32 >= -T - 1 and the span is shorter than 3 lines: at most two wraps
     int wi = p0 / 32 + (int)i;
-    wi %= (int)T;
     if (wi < 0) wi += (int)T;
+    if (wi < 0) wi += (int)T;
+    if (wi >= (int)T) wi -= (int)T;
+    if (wi >= (int)T) wi -= (int)T;
     w[i] = occ_line[wi];
   }
   __syncthreads();
@@ -218,9 +224,10 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_cmin(Group g, LineCfg lc,
     const bool live = bits_before(w, wpre, p + k) == bits_before(w, wpre, p);
     u64 v = KEY_NONE;
     if (live) {
+      // position x0 - (k-1) + u lies in [-(k-1), L + k - 1) with k <= L
       int pos = (int)x0 - (int)(k - 1) + (int)u;
-      pos %= (int)L;
       if (pos < 0) pos += (int)L;
+      else if (pos >= (int)L) pos -= (int)L;
       const u64 idx = F == 0 ? (u64)line * L + (u32)pos : g.LL + (u64)(u32)pos * L + line;
       v = g.keys ? g.keys[idx] : mix64(zb + SM_GAMMA * idx);
       any = true;
