@@ -239,6 +239,21 @@ struct rsa {
   int sm_count = 0;
   int tile_blocks[2] = {0, 0};  // resident blocks per SM: cmin, accept
   Prof prof;
+  // CUDA graphs of a chunk of greedy rounds and of bisection probes, captured
+  // once per (workspace, batch size, key source) on a private stream and
+  // replayed on the run's stream
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  // chunks the previous run needed before its samples were done: the next
+  // run launches that many before its first device->host check
+  u32 round_chunks_hint = 1, probe_chunks_hint = 1;
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    const void* ws = nullptr;
+    u32 n = 0;
+    bool keys = false;
+    unsigned long long launches[32] = {};
+  } g_round, g_probe;
 };
 
 namespace {
@@ -390,6 +405,52 @@ int launch_tile(rsa_t* h, Group g, TileCfg tc, u32* occw, u8* dead, const u32* t
   return 0;
 }
 
+void drop_graph(rsa_t::GraphSlot& gs) {
+  if (gs.exec) cudaGraphExecDestroy(gs.exec);
+  gs.exec = nullptr;
+  gs.ws = nullptr;
+}
+
+// Run `body(stream)` once, either directly or through a captured graph.
+template <typename B>
+int run_chunk(rsa_t* h, rsa_t::GraphSlot& gs, cudaStream_t stream, u32 n, B body) {
+  if (!h->use_graphs || h->prof.on) {
+    body(stream);
+    return launch_check("chunk launches");
+  }
+  if (!(gs.exec && gs.ws == h->ws && gs.n == n && gs.keys == h->with_keys)) {
+    drop_graph(gs);
+    if (!h->cap_stream)
+      CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    unsigned long long before[KD_COUNT];
+    std::memcpy(before, h->prof.launches, sizeof(before));
+    CUDA_TRY(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    body(h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RSA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&gs.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      gs.exec = nullptr;
+      return fail(RSA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < KD_COUNT; ++i) {
+      gs.launches[i] = h->prof.launches[i] - before[i];
+      h->prof.launches[i] = before[i];
+    }
+    gs.ws = h->ws;
+    gs.n = n;
+    gs.keys = h->with_keys;
+  }
+  CUDA_TRY(cudaGraphLaunch(gs.exec, stream));
+  for (int i = 0; i < KD_COUNT; ++i) h->prof.launches[i] += gs.launches[i];
+  return 0;
+}
+
 int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaStream_t stream) {
   if (n == 0) return fail(RSA_EINVAL, "n_samples must be >= 1");
   int rc;
@@ -450,41 +511,53 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   // every round accepts at least the smallest live key, so n_j + 1 rounds
   // always suffice
   const u32 round_cap = cap_nodes_of(h->L, h->k) + 2;
-  for (u32 r = 0;; ++r) {
-    CUDA_TRY(cudaMemsetAsync(d_counter, 0, 4, stream));
-    if (G.tile) {
-      if ((rc = launch_tile(h, g, tc, occw, dead, tgrid, stream))) return rc;
-    } else if (G.line) {
-      u32* occT = reinterpret_cast<u32*>(b + l.occT);
-      u64* cB = reinterpret_cast<u64*>(b + l.cB);
-      const dim3 lg(h->L * G.lc.nseg, n), tg(G.tc.T2, n);
-      launch(h, KD_LINE_CMIN_H, k_line_cmin<0>, lg, dim3(LINE_THREADS), G.line_smem, stream, g,
-             G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
-      launch(h, KD_LINE_CMIN_V, k_line_cmin<1>, lg, dim3(LINE_THREADS), G.line_smem, stream, g,
-             G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
-      launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, stream, g, g.cmin, cB);
-      launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_smem, stream,
-             g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
-      launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_smem, stream,
-             g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
-    } else {
-      launch(h, KD_ROW_CMIN, k_row<0>, rg, dim3(G.row_threads), G.row_smem, stream, g, G.row);
-      launch(h, KD_COL_CMIN, k_col<0>, cg, dim3(G.col_threads), G.col_smem, stream, g, G.col);
-      launch(h, KD_ROW_ACCEPT, k_row<1>, rg, dim3(G.row_threads), G.row_smem, stream, g, G.row);
-      launch(h, KD_COL_ACCEPT, k_col<1>, cg, dim3(G.col_threads), G.col_smem, stream, g, G.col);
+  // one chunk = ROUND_CHECK greedy rounds; k_round_end counts the samples
+  // still active after each round into d_counter
+  u32* occT = reinterpret_cast<u32*>(b + l.occT);
+  u64* cB = reinterpret_cast<u64*>(b + l.cB);
+  int body_rc = 0;
+  auto rounds = [&](cudaStream_t st) {
+    for (u32 i = 0; i < ROUND_CHECK; ++i) {
+      if (cudaMemsetAsync(d_counter, 0, 4, st) != cudaSuccess) body_rc = RSA_ECUDA;
+      if (G.tile) {
+        if (launch_tile(h, g, tc, occw, dead, tgrid, st)) body_rc = RSA_EINVAL;
+      } else if (G.line) {
+        const dim3 lg(h->L * G.lc.nseg, n), tg(G.tc.T2, n);
+        launch(h, KD_LINE_CMIN_H, k_line_cmin<0>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
+               G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
+        launch(h, KD_LINE_CMIN_V, k_line_cmin<1>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
+               G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
+        launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, st, g, g.cmin, cB);
+        launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
+               G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
+        launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
+               G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
+      } else {
+        launch(h, KD_ROW_CMIN, k_row<0>, rg, dim3(G.row_threads), G.row_smem, st, g, G.row);
+        launch(h, KD_COL_CMIN, k_col<0>, cg, dim3(G.col_threads), G.col_smem, st, g, G.col);
+        launch(h, KD_ROW_ACCEPT, k_row<1>, rg, dim3(G.row_threads), G.row_smem, st, g, G.row);
+        launch(h, KD_COL_ACCEPT, k_col<1>, cg, dim3(G.col_threads), G.col_smem, st, g, G.col);
+      }
+      launch(h, KD_ROUND_END, k_round_end, dim3((n + 127) / 128), dim3(128), 0, st, g, round_cap,
+             d_counter);
     }
-    launch(h, KD_ROUND_END, k_round_end, dim3((n + 127) / 128), dim3(128), 0, stream, g,
-           round_cap, d_counter);
-    if ((rc = launch_check("round kernels"))) return rc;
-    if ((r + 1) % ROUND_CHECK == 0) {
-      u32 active;
-      if ((rc = read_counter(h, d_counter, &active))) return rc;
-      if (active == 0) break;
+  };
+  for (u32 chunks = 0;;) {
+    const u32 burst = chunks == 0 ? h->round_chunks_hint : 1;
+    for (u32 i = 0; i < burst; ++i, ++chunks)
+      if ((rc = run_chunk(h, h->g_round, stream, n, rounds))) return rc;
+    if (body_rc) return fail(body_rc, "round launches failed");
+    u32 active;
+    if ((rc = read_counter(h, d_counter, &active))) return rc;
+    if (active == 0) {
+      h->round_chunks_hint = chunks;
+      break;
     }
   }
   // contact graph of the jammed lattice
   {
-    u32 bx = (u32)std::min<u64>((LL + 255) / 256, 4096);
+    // rows per sample spread over enough blocks to fill the GPU across the batch
+    const u32 bx = (u32)std::min<u64>(h->L, std::max<u64>(1, 65536 / n));
     launch(h, KD_EDGES, k_edges, dim3(bx, n), dim3(256), 0, stream, g);
     if ((rc = launch_check("k_edges"))) return rc;
   }
@@ -500,17 +573,25 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   const u64 per_sample = std::max<u64>(8, 16384 / n);
   const u32 copy_bx = (u32)std::min<u64>(((u64)g.cap_nodes + 255) / 256, per_sample);
   const u32 probe_bx = (u32)std::min<u64>(((u64)g.cap_edges + 255) / 256, per_sample);
-  for (u32 p = 0; p < PROBE_CAP + 1; ++p) {
-    CUDA_TRY(cudaMemsetAsync(d_counter + 1, 0, 4, stream));
-    launch(h, KD_PROBE_COPY, k_probe_copy, dim3(copy_bx, n), dim3(256), 0, stream, g);
-    launch(h, KD_PROBE, k_probe, dim3(probe_bx, n), dim3(256), 0, stream, g);
-    launch(h, KD_DECIDE, k_search_decide, dim3((n + 127) / 128), dim3(128), 0, stream, g,
-           (u32)PROBE_CAP, d_counter + 1);
-    if ((rc = launch_check("probe kernels"))) return rc;
-    if ((p + 1) % PROBE_CHECK == 0) {
-      u32 open;
-      if ((rc = read_counter(h, d_counter + 1, &open))) return rc;
-      if (open == 0) break;
+  auto probes = [&](cudaStream_t st) {
+    for (u32 i = 0; i < PROBE_CHECK; ++i) {
+      if (cudaMemsetAsync(d_counter + 1, 0, 4, st) != cudaSuccess) body_rc = RSA_ECUDA;
+      launch(h, KD_PROBE_COPY, k_probe_copy, dim3(copy_bx, n), dim3(256), 0, st, g);
+      launch(h, KD_PROBE, k_probe, dim3(probe_bx, n), dim3(256), 0, st, g);
+      launch(h, KD_DECIDE, k_search_decide, dim3((n + 127) / 128), dim3(128), 0, st, g,
+             (u32)PROBE_CAP, d_counter + 1);
+    }
+  };
+  for (u32 chunks = 0; chunks * PROBE_CHECK < PROBE_CAP + PROBE_CHECK;) {
+    const u32 burst = chunks == 0 ? h->probe_chunks_hint : 1;
+    for (u32 i = 0; i < burst; ++i, ++chunks)
+      if ((rc = run_chunk(h, h->g_probe, stream, n, probes))) return rc;
+    if (body_rc) return fail(body_rc, "probe launches failed");
+    u32 open;
+    if ((rc = read_counter(h, d_counter + 1, &open))) return rc;
+    if (open == 0) {
+      h->probe_chunks_hint = chunks;
+      break;
     }
   }
   // tile-pass work counters of this run (for throughput accounting)
@@ -639,6 +720,7 @@ int rsa_run_static(uint32_t L, uint32_t k, const uint64_t* seeds, uint32_t n, ui
   void* ws = nullptr;
   int rc = static_workspace(&ws);
   if (rc) return rc;
+  h.use_graphs = false;  // plain launches only: nothing is created or allocated
   h.bound_ptr = ws;  // the run's buffers (all re-initialised by the run) live here
   h.bound_bytes = STATIC_WS_BYTES;
   alignas(8) u32 counter[16] = {};  // pageable host words for the loop checks
@@ -778,6 +860,9 @@ const char* rsa_kernel_name(uint32_t kind) {
 
 void rsa_destroy(rsa_t* h) {
   if (!h) return;
+  drop_graph(h->g_round);
+  drop_graph(h->g_probe);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   if (h->own_ptr) cudaFree(h->own_ptr);
   if (h->h_counter) cudaFreeHost(h->h_counter);

@@ -230,26 +230,18 @@ __device__ __forceinline__ u32 pos_in_kmer(u32 pos, u32 cy, u32 cx, u32 L, u32* 
   return (int)d < 0 ? d + L : d;
 }
 
-__device__ __forceinline__ bool contact(const Group& g, u32 s, u32 y, u32 x, u32 dir, u32* m1,
-                                        u32* m2, u32* dxy) {
-  const u32 L = g.L;
-  const u32* own = g.owner + (size_t)s * g.LL;
-  const u32 a = own[(size_t)y * L + x];
-  if (a == NONE32) return false;
-  const u32 by = dir ? (y + 1 == L ? 0 : y + 1) : y;
-  const u32 bx = dir ? x : (x + 1 == L ? 0 : x + 1);
-  const u32 b = own[(size_t)by * L + bx];
-  if (b == NONE32) return false;
+// Lifted displacement of the contact between cell (y, x) of node m1 and its
+// neighbour (by, bx) in direction dir of node m2, packed as 16+16 bits.
+__device__ __forceinline__ u32 contact_delta(const Group& g, u32 s, u32 y, u32 x, u32 by, u32 bx,
+                                             u32 dir, u32 m1, u32 m2, bool* internal) {
   const u32* npos = g.node_pos + (size_t)s * g.cap_nodes;
   u32 o1, o2;
-  const u32 i = pos_in_kmer(npos[a], y, x, L, &o1);
-  const u32 j = pos_in_kmer(npos[b], by, bx, L, &o2);
+  const u32 i = pos_in_kmer(npos[m1], y, x, g.L, &o1);
+  const u32 j = pos_in_kmer(npos[m2], by, bx, g.L, &o2);
   const int dx = (o1 == 0 ? (int)i : 0) + (dir == 0) - (o2 == 0 ? (int)j : 0);
   const int dy = (o1 == 1 ? (int)i : 0) + (dir == 1) - (o2 == 1 ? (int)j : 0);
-  *m1 = a;
-  *m2 = b;
-  *dxy = ((u32)dx & 0xFFFFu) | (((u32)dy & 0xFFFFu) << 16);
-  return !(a == b && dx == 0 && dy == 0);
+  *internal = m1 == m2 && dx == 0 && dy == 0;
+  return ((u32)dx & 0xFFFFu) | (((u32)dy & 0xFFFFu) << 16);
 }
 
 __global__ void k_edges(Group g) {
@@ -257,26 +249,50 @@ __global__ void k_edges(Group g) {
   const u32 L = g.L;
   const u32 lane = threadIdx.x & 31;
   SampleState& st = g.st[s];
+  const u32* own = g.owner + (size_t)s * g.LL;
   const u64* nkey = g.node_key + (size_t)s * g.cap_nodes;
   Edge* E = g.edges + (size_t)s * g.cap_edges;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  // every lane of a warp runs the same number of iterations (ballots below)
-  const u64 iters = (g.LL + stride - 1) / stride;
-  for (u64 it = 0; it < iters; ++it) {
-    const u64 c = it * stride + (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool inb = c < g.LL;
-    const u32 y = inb ? (u32)(c / L) : 0, x = inb ? (u32)(c % L) : 0;
+  // For k < L (and L > 2) consecutive contacts between the same two k-mers
+  // along a run always have the same displacement, so runs are told apart by
+  // their owners alone; rings (k = L) and tiny lattices compare displacements.
+  const bool full_compare = g.k == L || L <= 2;
+  // block b walks rows b, b + gridDim.x, ...; its threads stride along the
+  // row (every lane of a warp runs the same number of steps: ballots below)
+  const u32 xsteps = (L + blockDim.x - 1) / blockDim.x;
+  for (u32 y = blockIdx.x; y < L; y += gridDim.x)
+  for (u32 xs = 0; xs < xsteps; ++xs) {
+    const u32 xx = xs * blockDim.x + threadIdx.x;
+    const bool inb = xx < L;
+    const u32 x = inb ? xx : 0;
+    const u32 yp = y == 0 ? L - 1 : y - 1, yn = y + 1 == L ? 0 : y + 1;
+    const u32 xp = x == 0 ? L - 1 : x - 1, xn = x + 1 == L ? 0 : x + 1;
+    const u32 a = inb ? own[(size_t)y * L + x] : NONE32;
 #pragma unroll
     for (u32 dir = 0; dir < 2; ++dir) {
-      u32 m1 = 0, m2 = 0, d = 0;
-      bool emit = inb && contact(g, s, y, x, dir, &m1, &m2, &d);
-      if (emit) {
-        const bool force = dir == 0 ? (y == 0) : (x == 0);
-        if (!force) {
-          const u32 py = dir == 0 ? y - 1 : y, px = dir == 0 ? x : x - 1;
-          u32 p1, p2, pd;
-          if (contact(g, s, py, px, dir, &p1, &p2, &pd) && p1 == m1 && p2 == m2 && pd == d)
-            emit = false;
+      const u32 by = dir ? yn : y, bx = dir ? x : xn;
+      bool emit = false;
+      u32 b = NONE32, d = 0;
+      if (a != NONE32) {
+        b = own[(size_t)by * L + bx];
+        if (b != NONE32) {
+          bool internal = false;
+          // the previous contact of the run: one row up (+x edges) or one
+          // column left (+y edges)
+          const bool force = dir == 0 ? (y == 0) : (x == 0);
+          const u32 py = dir == 0 ? yp : y, px = dir == 0 ? x : xp;
+          const u32 qy = dir == 0 ? yp : yn, qx = dir == 0 ? xn : xp;
+          const u32 pa = force ? NONE32 : own[(size_t)py * L + px];
+          const u32 pb = force ? NONE32 : own[(size_t)qy * L + qx];
+          const bool same_pair = pa == a && pb == b;
+          if (!same_pair || full_compare) {
+            d = contact_delta(g, s, y, x, by, bx, dir, a, b, &internal);
+            emit = !internal;
+            if (emit && same_pair) {
+              bool pint = false;
+              const u32 pd = contact_delta(g, s, py, px, qy, qx, dir, pa, pb, &pint);
+              emit = pd != d;
+            }
+          }
         }
       }
       const u32 mask = __ballot_sync(FULL, emit);
@@ -289,9 +305,9 @@ __global__ void k_edges(Group g) {
         const u32 e = basei + __popc(mask & ((1u << lane) - 1u));
         if (e < g.cap_edges) {
           Edge ed;
-          ed.time = max(nkey[m1], nkey[m2]);
-          ed.m1 = m1;
-          ed.m2 = m2;
+          ed.time = max(nkey[a], nkey[b]);
+          ed.m1 = a;
+          ed.m2 = b;
           ed.dxy = d;
           ed.pad = 0;
           E[e] = ed;
