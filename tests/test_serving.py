@@ -1,0 +1,114 @@
+"""Continuous-batching scheduler (host logic on CPU with a fake runner) and
+the served path on the GPU: every job's results are identical alone and in
+a mix, and match the oracle."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1810_06800_gb300 import serve
+
+
+def _fake_ws(L, k, n):
+    return L * L * n
+
+
+def _fake_runner(log, lock, delay=0.002):
+    def run(L, k, seeds, nbytes, w):
+        with lock:
+            log.append(("start", w, nbytes))
+        time.sleep(delay)
+        # deterministic stand-in results: functions of (L, k, seed) only
+        s = seeds.astype(np.uint64)
+        nj = ((s * np.uint64(2654435761) + np.uint64(L * 131 + k)) % np.uint64(1000)).astype(np.uint32)
+        nc = (nj // 2).astype(np.uint32)
+        with lock:
+            log.append(("end", w, nbytes))
+        return nj, nc
+    return run
+
+
+def _expected(L, k, seed, n):
+    s = np.arange(seed, seed + n, dtype=np.uint64)
+    nj = ((s * np.uint64(2654435761) + np.uint64(L * 131 + k)) % np.uint64(1000)).astype(np.uint32)
+    return nj, (nj // 2).astype(np.uint32)
+
+
+def test_scheduler_splits_batches_and_respects_the_budget():
+    log, lock = [], threading.Lock()
+    budget = 64 * 64 * 10          # ten 64x64 samples in flight at most
+    sch = serve.Scheduler(_fake_runner(log, lock), _fake_ws, budget, workers=3, max_batch=8)
+    jobs = [sch.submit(serve.Job(i, L, k, n, seed))
+            for i, (L, k, n, seed) in enumerate([(64, 4, 30, 1), (32, 2, 5, 100), (64, 8, 17, 7),
+                                                 (16, 1, 40, 3)])]
+    for j in jobs:
+        assert j.done_event.wait(10)
+    sch.close()
+    for j in jobs:
+        wj, wc = _expected(j.L, j.k, j.seed, j.n)
+        assert np.array_equal(j.nj, wj) and np.array_equal(j.nc, wc)
+    # in-flight workspace never exceeded the budget, and batches overlapped
+    inflight = peak = 0
+    for ev, _, b in log:
+        inflight += b if ev == "start" else -b
+        peak = max(peak, inflight)
+    assert peak <= budget
+    st = sch.stats()
+    assert st["done"] == 4 and st["peak_in_flight_bytes"] <= budget
+    assert st["peak_concurrent_batches"] >= 2
+
+
+def test_batch_size_shrinks_to_fit_the_budget():
+    sch = serve.Scheduler(lambda *a: None, _fake_ws, budget_bytes=1024 * 1024 * 3, workers=1,
+                          max_batch=256)
+    assert sch.batch_size(1024, 32, 100) == 2   # 1 MiB per sample, 3 MiB budget
+    with pytest.raises(MemoryError):
+        sch.batch_size(4096, 32, 1)
+    sch.close()
+
+
+def test_job_alone_and_in_a_mix_agree_fake():
+    log, lock = [], threading.Lock()
+    specs = [(64, 4, 12, 5), (32, 2, 9, 50), (128, 8, 6, 9)]
+    alone = []
+    for i, (L, k, n, seed) in enumerate(specs):
+        sch = serve.Scheduler(_fake_runner(log, lock), _fake_ws, 10**9, workers=1, max_batch=4)
+        j = sch.submit(serve.Job(i, L, k, n, seed))
+        j.done_event.wait(10)
+        sch.close()
+        alone.append((j.nj.copy(), j.nc.copy()))
+    sch = serve.Scheduler(_fake_runner(log, lock), _fake_ws, 10**9, workers=3, max_batch=4)
+    mixed = [sch.submit(serve.Job(i, *sp)) for i, sp in enumerate(specs)]
+    for j in mixed:
+        j.done_event.wait(10)
+    sch.close()
+    for (aj, ac), j in zip(alone, mixed):
+        assert np.array_equal(aj, j.nj) and np.array_equal(ac, j.nc)
+
+
+@pytest.mark.gpu
+def test_served_jobs_alone_and_in_a_mix_match():
+    import oracle
+    from paper_1810_06800_gb300 import rsa
+    specs = [(64, 4, 24, 1), (96, 16, 10, 300), (128, 64, 6, 77), (100, 3, 8, 9), (32, 2, 40, 5)]
+    alone = []
+    for L, k, n, seed in specs:
+        lat = rsa.Lattice(L, k)
+        alone.append(lat.run(np.arange(seed, seed + n, dtype=np.uint64)))
+        lat.close()
+    sch = serve.make_server(workers=3, budget_bytes=256 << 20, max_batch=8)
+    jobs = [sch.submit(serve.Job(i, *sp)) for i, sp in enumerate(specs)]
+    for j in jobs:
+        assert j.done_event.wait(120)
+    sch.close()
+    sch.gpu_runner.close()
+    for (aj, ac), j in zip(alone, jobs):
+        assert j.error is None
+        assert np.array_equal(aj, j.nj) and np.array_equal(ac, j.nc)
+    assert sch.stats()["peak_concurrent_batches"] >= 2
+    # and the oracle agrees on a few samples of each job
+    for j in jobs:
+        for i in range(min(3, j.n)):
+            wj, wc, _ = oracle.sample(j.L, j.k, j.seed + i)
+            assert (int(j.nj[i]), int(j.nc[i])) == (wj, wc)
