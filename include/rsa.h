@@ -101,6 +101,14 @@ int rsa_results(rsa_t *h, uint32_t *n_j, uint32_t *n_c, uint32_t n);
 int rsa_sample_stats(rsa_t *h, uint32_t *rounds, uint32_t *probes, uint32_t *edges,
                      int32_t *status, uint32_t n);
 
+/* Interspecific contacts at jamming (Sec. II.A, Eq. nxy: n_xy* =
+ * n_xy / (n_x + n_y + n_xy)) for each of the last run's first n samples.
+ * A contact is a lattice edge (4-neighbour pair on the torus) whose two
+ * sites belong to different k-mers; n_x counts those between two horizontal
+ * k-mers, n_y between two vertical ones, n_xy between perpendicular ones.
+ * Host arrays of length n (any may be NULL). */
+int rsa_contacts(rsa_t *h, uint32_t *n_x, uint32_t *n_y, uint32_t *n_xy, uint32_t n);
+
 /* TEST ONLY: the accepted candidates (idx) of sample `sample` of the last run,
  * sorted ascending; *count receives n_j; at most cap values are written. */
 int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_t *count);

@@ -72,6 +72,10 @@ def _load():
     lib.oracle_sample_keys.argtypes = [u32, u32, vp, i64p, i64p, i64p, vp]
     lib.oracle_is_jammed.restype = ctypes.c_int
     lib.oracle_is_jammed.argtypes = [u32, u32, vp]
+    lib.oracle_contacts.restype = ctypes.c_int
+    lib.oracle_contacts.argtypes = [u32, u32, vp, ctypes.c_int64, i64p, i64p, i64p]
+    lib.oracle_max_free_runs.restype = None
+    lib.oracle_max_free_runs.argtypes = [u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     _lib = lib
     return lib
 
@@ -153,6 +157,40 @@ def sample_keys(L: int, k: int, key_arr: np.ndarray):
 def is_jammed(L: int, k: int, occ: np.ndarray) -> bool:
     occ = np.ascontiguousarray(occ, dtype=np.uint8)
     return bool(_load().oracle_is_jammed(L, k, occ.ctypes.data))
+
+
+def contacts(L: int, k: int, accepted):
+    """Interspecific contacts (n_x, n_y, n_xy) of a configuration (Sec. II.A)."""
+    acc = np.ascontiguousarray(accepted, dtype=np.uint32)
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = _load().oracle_contacts(L, k, acc.ctypes.data, acc.size, ctypes.byref(a),
+                                 ctypes.byref(b), ctypes.byref(c))
+    if rc != 0:
+        raise MemoryError("oracle_contacts failed")
+    return int(a.value), int(b.value), int(c.value)
+
+
+def max_free_runs(occ: np.ndarray):
+    """(longest free run along rows, along columns), circular; the lattice is
+    jammed for k-mers iff both are < k.  O(L^2), usable at any size."""
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    L = occ.shape[0]
+    h, v = ctypes.c_uint32(), ctypes.c_uint32()
+    _load().oracle_max_free_runs(L, occ.ctypes.data, ctypes.byref(h), ctypes.byref(v))
+    return int(h.value), int(v.value)
+
+
+def occupancy_from_accepted(L: int, k: int, accepted) -> np.ndarray:
+    """uint8[L, L] occupancy of the given accepted candidates (idx)."""
+    occ = np.zeros((L, L), dtype=np.uint8)
+    acc = np.asarray(accepted, dtype=np.int64)
+    o, r = np.divmod(acc, L * L)
+    y, x = np.divmod(r, L)
+    for i in range(k):
+        h = o == 0
+        occ[y[h], (x[h] + i) % L] += 1
+        occ[(y[~h] + i) % L, x[~h]] += 1
+    return occ
 
 
 def samples(L: int, k: int, seeds, threads: int = 1):

@@ -148,3 +148,25 @@ def maximal_packings(L: int, k: int):
 
     rec(0, frozenset())
     return found
+
+
+def contacts(L: int, k: int, accepted):
+    """Interspecific contacts by brute force: every unordered pair of
+    4-adjacent occupied cells of different k-mers, once per lattice edge
+    (so L = 2 counts both edges of a pair), classified by orientations."""
+    owner = {}
+    for m, idx in enumerate(accepted):
+        for c in cells_of(L, k, int(idx)):
+            owner[c] = (m, int(idx) >= L * L)
+    nx = ny = nxy = 0
+    for (y, x), (m, vert) in owner.items():
+        for b in (((y + 1) % L, x), (y, (x + 1) % L)):
+            if b in owner and owner[b][0] != m:
+                ob = owner[b][1]
+                if ob != vert:
+                    nxy += 1
+                elif vert:
+                    ny += 1
+                else:
+                    nx += 1
+    return nx, ny, nxy

@@ -306,3 +306,66 @@ int oracle_is_jammed(uint32_t L, uint32_t k, const uint8_t *occ)
     }
     return 1;
 }
+
+/* Longest circular run of free cells along any row (horizontal) or column
+ * (vertical) of an L x L occupancy map.  The lattice is jammed for k-mers iff
+ * both are < k (a free run of k cells is exactly a placeable k-mer). */
+void oracle_max_free_runs(uint32_t L, const uint8_t *occ, uint32_t *hrun, uint32_t *vrun)
+{
+    uint32_t hmax = 0, vmax = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        uint32_t best = 0;
+        for (uint32_t line = 0; line < L; ++line) {
+            /* walk the line twice to see runs that wrap round it */
+            uint32_t run = 0, all_free = 1;
+            for (uint32_t t = 0; t < 2 * L; ++t) {
+                uint32_t i = t % L;
+                uint8_t o = dir == 0 ? occ[(size_t)line * L + i] : occ[(size_t)i * L + line];
+                if (o) { run = 0; all_free = 0; }
+                else if (++run > best) best = run;
+            }
+            if (all_free) best = L;  /* an empty line holds any k <= L */
+        }
+        if (best > L) best = L;
+        if (dir == 0) hmax = best; else vmax = best;
+    }
+    *hrun = hmax;
+    *vrun = vmax;
+}
+
+/* Interspecific contacts (Sec. II.A, Eq. nxy): over every lattice edge
+ * (cell, cell + x) and (cell, cell + y) of the torus whose two cells are
+ * occupied by different k-mers, count the pairs of two horizontal k-mers
+ * (nx), two vertical ones (ny) and perpendicular ones (nxy). */
+int oracle_contacts(uint32_t L, uint32_t k, const uint32_t *accepted, int64_t nj,
+                    int64_t *nx, int64_t *ny, int64_t *nxy)
+{
+    size_t LL = (size_t)L * L;
+    int64_t *who = (int64_t *)malloc(LL * sizeof(int64_t));
+    if (!who) return -2;
+    for (size_t i = 0; i < LL; ++i) who[i] = -1;
+    for (int64_t m = 0; m < nj; ++m)
+        for (uint32_t i = 0; i < k; ++i) {
+            uint32_t y, x;
+            orc_cell(L, accepted[m], i, &y, &x);
+            who[(size_t)y * L + x] = m;
+        }
+    int64_t cx = 0, cy = 0, cxy = 0;
+    for (uint32_t y = 0; y < L; ++y)
+        for (uint32_t x = 0; x < L; ++x) {
+            int64_t a = who[(size_t)y * L + x];
+            if (a < 0) continue;
+            int64_t nb[2] = {who[(size_t)y * L + (x + 1) % L], who[(size_t)((y + 1) % L) * L + x]};
+            for (int d = 0; d < 2; ++d) {
+                int64_t b = nb[d];
+                if (b < 0 || b == a) continue;
+                int oa = accepted[a] >= LL, ob = accepted[b] >= LL;   /* 1 = vertical */
+                if (oa != ob) ++cxy;
+                else if (oa) ++cy;
+                else ++cx;
+            }
+        }
+    free(who);
+    *nx = cx; *ny = cy; *nxy = cxy;
+    return 0;
+}

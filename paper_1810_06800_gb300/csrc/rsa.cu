@@ -782,6 +782,20 @@ int rsa_sample_stats(rsa_t* h, uint32_t* rounds, uint32_t* probes, uint32_t* edg
   return 0;
 }
 
+int rsa_contacts(rsa_t* h, uint32_t* n_x, uint32_t* n_y, uint32_t* n_xy, uint32_t n) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  if (n > h->last_n) return fail(RSA_EINVAL, "n exceeds samples of the last run");
+  std::vector<SampleState> st;
+  int rc = fetch_states(h, st);
+  if (rc) return rc;
+  for (u32 i = 0; i < n; ++i) {
+    if (n_x) n_x[i] = st[i].contacts_x;
+    if (n_y) n_y[i] = st[i].contacts_y;
+    if (n_xy) n_xy[i] = st[i].contacts_xy;
+  }
+  return 0;
+}
+
 int rsa_accepted(rsa_t* h, uint32_t sample, uint32_t* idx, uint32_t cap, uint32_t* count) {
   if (!h || !count) return fail(RSA_EINVAL, "null argument");
   if (sample >= h->last_n) return fail(RSA_EINVAL, "sample out of range");

@@ -64,7 +64,9 @@ struct SampleState {   // one per sample, 128 bytes
   u64 lo, hi, mid;
   u32 cnt_lo, cnt_hi, cnt_mid, lo_valid;
   u32 cur, sdone, nc, hi_ok;
-  u32 pad[10];
+  u32 contacts_x, contacts_y, contacts_xy;  // lattice edges between different
+                                            // k-mers: both H, both V, mixed
+  u32 pad[7];
 };
 
 struct Group {         // one batch of samples sharing (L, k)

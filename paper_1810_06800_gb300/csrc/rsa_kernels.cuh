@@ -272,8 +272,14 @@ __global__ void k_edges(Group g) {
       const u32 by = dir ? yn : y, bx = dir ? x : xn;
       bool emit = false;
       u32 b = NONE32, d = 0;
+      u32 kind = 3;  // contact class: 0 both horizontal, 1 both vertical, 2 mixed
       if (a != NONE32) {
         b = own[(size_t)by * L + bx];
+        if (b != NONE32 && b != a) {
+          const u32* npos = g.node_pos + (size_t)s * g.cap_nodes;
+          const u32 oa = npos[a] >> 31, ob = npos[b] >> 31;
+          kind = oa != ob ? 2u : oa;
+        }
         if (b != NONE32) {
           bool internal = false;
           // the previous contact of the run: one row up (+x edges) or one
@@ -294,6 +300,15 @@ __global__ void k_edges(Group g) {
             }
           }
         }
+      }
+      // interspecific-contact counts (Sec. II.A): every contact, before the
+      // run deduplication of the graph edges
+#pragma unroll
+      for (u32 c = 0; c < 3; ++c) {
+        const u32 m = __ballot_sync(FULL, kind == c);
+        if (m && lane == __ffs(m) - 1)
+          atomicAdd(c == 0 ? &st.contacts_x : c == 1 ? &st.contacts_y : &st.contacts_xy,
+                    (u32)__popc(m));
       }
       const u32 mask = __ballot_sync(FULL, emit);
       if (!mask) continue;

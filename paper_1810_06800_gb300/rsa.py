@@ -21,7 +21,7 @@ _NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_EC
           RSA_ETIMEOUT: "RSA_ETIMEOUT", RSA_ENOWRAP: "RSA_ENOWRAP", RSA_ESTATE: "RSA_ESTATE"}
 SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_run_static",
            "rsa_results",
-           "rsa_sample_stats", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
+           "rsa_sample_stats", "rsa_contacts", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
            "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
@@ -55,6 +55,7 @@ def load():
     lib.rsa_run_static.argtypes = [u32, u32, vp, u32, vp, vp, vp]
     lib.rsa_results.argtypes = [vp, vp, vp, u32]
     lib.rsa_sample_stats.argtypes = [vp, vp, vp, vp, vp, u32]
+    lib.rsa_contacts.argtypes = [vp, vp, vp, vp, u32]
     lib.rsa_accepted.argtypes = [vp, u32, vp, u32, ctypes.POINTER(u32)]
     lib.rsa_workspace_bytes.argtypes = [u32, u32, u32, ctypes.POINTER(u64)]
     lib.rsa_bind_workspace.argtypes = [vp, vp, u64]
@@ -142,6 +143,15 @@ def rsa_sample_stats(h, n: int):
     return dict(rounds=r, probes=p, edges=e, status=s)
 
 
+def rsa_contacts(h, n: int):
+    """(n_x, n_y, n_xy) uint32 arrays of the last run's first n samples."""
+    a = np.zeros(n, dtype=np.uint32)
+    b = np.zeros(n, dtype=np.uint32)
+    c = np.zeros(n, dtype=np.uint32)
+    _check(load().rsa_contacts(h, a.ctypes.data, b.ctypes.data, c.ctypes.data, n))
+    return a, b, c
+
+
 def rsa_accepted(h, sample: int):
     cnt = ctypes.c_uint32()
     _check(load().rsa_accepted(h, sample, None, 0, ctypes.byref(cnt)))
@@ -221,6 +231,9 @@ class Lattice:
 
     def stats(self, n):
         return rsa_sample_stats(self.h, n)
+
+    def contacts(self, n):
+        return rsa_contacts(self.h, n)
 
     def accepted(self, sample=0):
         return rsa_accepted(self.h, sample)

@@ -33,6 +33,18 @@ def _check(L, k, seeds, configs=0):
     return nj, nc
 
 
+@pytest.mark.parametrize("L,k", [(64, 4), (96, 16), (100, 3), (128, 64), (1024, 32)])
+def test_interspecific_contacts(L, k):
+    seeds = list(range(1, 5))
+    lat = rsa.Lattice(L, k)
+    lat.run(seeds)
+    nx, ny, nxy = lat.contacts(len(seeds))
+    for i, s in enumerate(seeds):
+        acc, _ = oracle.scan(L, k, oracle.keys(L, s))
+        assert (int(nx[i]), int(ny[i]), int(nxy[i])) == oracle.contacts(L, k, acc)
+    lat.close()
+
+
 def test_plain_small_config_all_seeds():
     w = workloads.PLAIN_SMALL
     _check(w["L"], w["k"], w["seeds"], configs=10)
@@ -174,4 +186,28 @@ def test_invariants_at_scale():
     pj, pc = k * nj / L**2, k * nc / L**2
     assert abs(pj.mean() - 0.6892) < 0.01
     assert abs(pc.mean() - 0.4733) < 0.05
+    lat.close()
+
+
+@pytest.mark.parametrize("L,k,n", [(32768, 4096, 2), (8192, 512, 4)])
+def test_full_size_properties(L, k, n):
+    """Full-size configs the oracle cannot run whole: every sample is jammed
+    (no free run of k cells on any line), n_c <= n_j <= L^2/k, no status
+    error, and p_j sits near Table I (k = 512: 0.6618, k = 4096: 0.6575 at
+    L/k = 100; these lattices have L/k = 8..16)."""
+    lat = rsa.Lattice(L, k)
+    nj, nc = lat.run(list(range(1, n + 1)))
+    st = lat.stats(n)
+    assert np.all(st["status"] == 0)
+    assert np.all(nc >= 1) and np.all(nc <= nj) and np.all(nj <= L * L // k)
+    for i in range(n):
+        acc = lat.accepted(i)
+        assert acc.size == nj[i]
+        occ = oracle.occupancy_from_accepted(L, k, acc)
+        assert occ.max() == 1                      # no overlaps (repeated
+        assert int(occ.sum(dtype=np.int64)) == k * int(nj[i])  # cells collapse)
+        h, v = oracle.max_free_runs(occ)
+        assert h < k and v < k                     # jammed
+    pj = k * nj / L**2
+    assert abs(pj.mean() - (0.6575 if k == 4096 else 0.6618)) < 0.03
     lat.close()

@@ -172,6 +172,20 @@ def test_scan_result_is_jammed(L, k):
                                                             kind="stable").tolist()))
 
 
+@pytest.mark.parametrize("L,k", [(5, 2), (8, 3), (16, 4), (21, 7), (12, 12)])
+def test_free_run_jamming_check_agrees_with_brute_force(L, k):
+    rng = np.random.default_rng(L * 100 + k)
+    for trial in range(40):
+        occ = (rng.random((L, L)) < rng.uniform(0.3, 0.95)).astype(np.uint8)
+        h, v = oracle.max_free_runs(occ)
+        assert (h < k and v < k) == oracle.is_jammed(L, k, occ)
+    for seed in (1, 2):
+        acc, occ = oracle.scan(L, k, oracle.keys(L, seed))
+        h, v = oracle.max_free_runs(occ)
+        assert h < k and v < k
+        assert np.array_equal(oracle.occupancy_from_accepted(L, k, acc), occ)
+
+
 def test_jamming_check_rejects_a_gap():
     occ = np.ones((6, 6), dtype=np.uint8)
     occ[2, 1:4] = 0
@@ -264,3 +278,17 @@ def test_table1_smoke(n):
     assert abs(pj.mean() - want_pj) < 0.012
     assert abs(pc.mean() - want_pc) < 0.05
     assert np.all(nc <= nj)
+
+
+@pytest.mark.parametrize("L,k", [(2, 1), (3, 2), (6, 2), (8, 3), (12, 4), (16, 16)])
+def test_contacts_match_brute_force_and_edge_count(L, k):
+    for seed in range(1, 9):
+        acc, occ = oracle.scan(L, k, oracle.keys(L, seed))
+        got = oracle.contacts(L, k, acc)
+        assert got == brute.contacts(L, k, acc)
+        # every occupied-occupied lattice edge is a contact or lies inside a
+        # k-mer (k - 1 inner edges each, k for a k = L ring)
+        edges = int(np.sum(occ & np.roll(occ, -1, axis=1)) + np.sum(occ & np.roll(occ, -1, axis=0)))
+        inner = acc.size * (k if k == L else k - 1)
+        if L > 2:
+            assert sum(got) == edges - inner
