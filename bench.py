@@ -292,6 +292,15 @@ def main():
     e2e = n * world * args.steps / wall
     assert np.array_equal(nj_h, nj) and np.array_equal(nc_h, nc)
 
+    # ---- the plain path: one sample per run call, for comparison ----
+    plain_n = 16
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(plain_n):
+        rsa.rsa_run_seeds(h, seeds[i:i + 1], stream)
+        rsa.rsa_results(h, 1)
+    plain_rate = plain_n / (time.perf_counter() - t0)
+
     if rank != 0:
         lat.close()
         if pg is not None:
@@ -365,6 +374,8 @@ def main():
         "sites_per_s": value * L * L,
         "e2e": {"value": e2e, "unit": "samples/s", "h2d_bytes_per_step": int(8 * n),
                 "d2h_bytes_per_step": int(128 * n)},
+        "plain_one_sample_per_launch": {"value": plain_rate, "unit": "samples/s",
+                                        "samples": plain_n},
         "gpu_launches": int(sum(v[1] for v in ours.values())),
         "roofline": roof,
         "kernels": kernel_table,

@@ -259,6 +259,7 @@ __global__ void k_edges(Group g) {
   // block b walks rows b, b + gridDim.x, ...; its threads stride along the
   // row (every lane of a warp runs the same number of steps: ballots below)
   const u32 xsteps = (L + blockDim.x - 1) / blockDim.x;
+  u32 cnt[3] = {0, 0, 0};
   for (u32 y = blockIdx.x; y < L; y += gridDim.x)
   for (u32 xs = 0; xs < xsteps; ++xs) {
     const u32 xx = xs * blockDim.x + threadIdx.x;
@@ -303,13 +304,9 @@ __global__ void k_edges(Group g) {
       }
       // interspecific-contact counts (Sec. II.A): every contact, before the
       // run deduplication of the graph edges
-#pragma unroll
-      for (u32 c = 0; c < 3; ++c) {
-        const u32 m = __ballot_sync(FULL, kind == c);
-        if (m && lane == __ffs(m) - 1)
-          atomicAdd(c == 0 ? &st.contacts_x : c == 1 ? &st.contacts_y : &st.contacts_xy,
-                    (u32)__popc(m));
-      }
+      cnt[0] += kind == 0;
+      cnt[1] += kind == 1;
+      cnt[2] += kind == 2;
       const u32 mask = __ballot_sync(FULL, emit);
       if (!mask) continue;
       u32 basei = 0;
@@ -331,6 +328,12 @@ __global__ void k_edges(Group g) {
         }
       }
     }
+  }
+#pragma unroll
+  for (u32 c = 0; c < 3; ++c) {
+    const u32 t = __reduce_add_sync(FULL, cnt[c]);
+    if (lane == 0 && t)
+      atomicAdd(c == 0 ? &st.contacts_x : c == 1 ? &st.contacts_y : &st.contacts_xy, t);
   }
 }
 
