@@ -42,17 +42,20 @@ METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
 # minimum, the acceptance passes read it.
 BYTES_PER_CELL = {"k_row_cmin": 9, "k_col_cmin": 17, "k_row_accept": 8, "k_col_accept": 8}
 # Integer-ALU kernels (the 32x32 tile path), counted in 32-bit lane
-# operations: a 64-bit minimum is 4 ops (two compares, two selects), a
-# width-k window minimum by van Herk / Gil-Werman is 3 minima per cell, a
-# liveness test of a candidate's k cells is 4 ops (shift, mask, compare of a
-# 64-bit word), a splitmix64 priority is 20 ops (64-bit add 2, three 64-bit
-# xor-shifts at 4, two 64-bit constant multiplies at 3).
+# operations: a 64-bit minimum is 4 ops (two compares, two selects) plus 1
+# when the argmin is tracked, a width-k window minimum by van Herk /
+# Gil-Werman is 3 minima per cell, a liveness test of a candidate's k cells
+# is 4 ops (shift, mask, compare of a 64-bit word), a splitmix64 priority is
+# 20 ops (64-bit add 2, three 64-bit xor-shifts at 4, two 64-bit constant
+# multiplies at 3).
 OPS_PER_KEY = 20
 OPS_PER_CELL = {
-    # horizontal and vertical window minima, their combination, two liveness tests
-    "k_tile_cmin": 2 * 3 * 4 + 4 + 2 * 4,
-    # two forward window minima, two liveness tests; plus a compare per key
-    "k_tile_accept": 2 * 3 * 4 + 2 * 4,
+    # horizontal and vertical argmin window minima, their combination into a
+    # one-byte code (min + select), two liveness tests
+    "k_tile_cmin": 2 * 3 * 5 + 6 + 2 * 4,
+    # per direction: "code is the start value" and "next code is this + 1"
+    # (two byte compares and an add); keys only for accepted candidates
+    "k_tile_accept": 2 * 3,
 }
 TILE_WORK = {"k_tile_cmin": ("cmin_cells", "cmin_keys"),
              "k_tile_accept": ("accept_cells", "accept_keys")}
@@ -323,7 +326,7 @@ def main():
     if dom in TILE_WORK:
         cells_key, keys_key = TILE_WORK[dom]
         cells, keys = work[cells_key], work[keys_key]
-        ops = cells * OPS_PER_CELL[dom] + keys * (OPS_PER_KEY + (4 if dom == "k_tile_accept" else 0))
+        ops = cells * OPS_PER_CELL[dom] + keys * OPS_PER_KEY
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) \
             if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
@@ -335,10 +338,11 @@ def main():
                 "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} int lanes x {sm_mhz:.0f} MHz",
                 "alg_ops_per_launch": ops / dom_launches,
                 "cells_per_launch": cells / dom_launches,
-                "hbm_view": {"alg_bytes_per_launch": 8.0 * cells / dom_launches,
-                             "achieved_gbs": 8.0 * cells / (dom_ms / 1e3) / 1e9,
+                # one argmin code byte per cell written (cmin) or read (accept)
+                "hbm_view": {"alg_bytes_per_launch": 1.0 * cells / dom_launches,
+                             "achieved_gbs": 1.0 * cells / (dom_ms / 1e3) / 1e9,
                              "peak_gbs": hbm_peak,
-                             "frac": 8.0 * cells / (dom_ms / 1e3) / 1e9 / hbm_peak}}
+                             "frac": 1.0 * cells / (dom_ms / 1e3) / 1e9 / hbm_peak}}
     elif dom in BYTES_PER_CELL:
         alg_bytes = BYTES_PER_CELL[dom] * passes * L * L
         achieved = alg_bytes / (dom_ms / 1e3) / 1e9

@@ -166,7 +166,7 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   l.cB = take(G.line ? n * LL * 8 : 0);
   l.dead = take(G.tile ? (size_t)n * G.tc.T2 : 0);
   l.owner = take(n * LL * 4);
-  l.cmin = take(n * LL * 8);
+  l.cmin = take(n * LL * (G.tile ? 1 : 8));  // tile path: one argmin code byte per cell
   l.base = take((size_t)n * 8);
   l.node_key = take(n * cn * 8);
   l.node_idx = take(n * cn * 4);
@@ -360,9 +360,9 @@ int read_counter(rsa_t* h, u32* dev_counter, u32* out) {
 
 template <int K>
 int tile_occ_k(rsa_t* h) {
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[0], k_tile_cmin<K>, 64, 0));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[0], k_tile_cmin<K>, TILE_THREADS, 0));
   CUDA_TRY(
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[1], k_tile_accept<K>, 64, 0));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[1], k_tile_accept<K>, TILE_THREADS, 0));
   return 0;
 }
 
@@ -386,8 +386,8 @@ int tile_occupancy(rsa_t* h) {
 template <int K>
 void launch_tile_k(rsa_t* h, Group g, TileCfg tc, u32* occw, u8* dead, const u32* tgrid,
                    cudaStream_t stream) {
-  launch(h, KD_TILE_CMIN, k_tile_cmin<K>, dim3(tgrid[0]), dim3(64), 0, stream, g, tc, occw, dead);
-  launch(h, KD_TILE_ACCEPT, k_tile_accept<K>, dim3(tgrid[1]), dim3(64), 0, stream, g, tc, occw,
+  launch(h, KD_TILE_CMIN, k_tile_cmin<K>, dim3(tgrid[0]), dim3(TILE_THREADS), 0, stream, g, tc, occw, dead);
+  launch(h, KD_TILE_ACCEPT, k_tile_accept<K>, dim3(tgrid[1]), dim3(TILE_THREADS), 0, stream, g, tc, occw,
          (const u8*)dead);
 }
 

@@ -106,7 +106,118 @@ __device__ __forceinline__ void line_fwd(u64* ln) {
   }
 }
 
+// K = 32 variants of line_bwd / line_fwd that keep the suffix minima in the
+// shared-memory line itself instead of 32 64-bit registers (one block per
+// line, so no second block's values need to survive).
+__device__ __forceinline__ void line_bwd32_smem(u64* ln) {
+  u64 q = KEY_NONE;
+#pragma unroll 8
+  for (int j = 31; j >= 1; --j) {
+    q = tmin(q, ln[j]);
+    ln[j] = q;
+  }
+  u64 P = KEY_NONE;
+#pragma unroll 8
+  for (int i = 0; i < 31; ++i) {
+    P = tmin(P, ln[32 + i]);
+    ln[32 + i] = tmin(ln[i + 1], P);
+  }
+  ln[63] = tmin(P, ln[63]);
+}
+
+__device__ __forceinline__ void line_fwd32_smem(u64* ln) {
+  u64 q = ln[31];
+#pragma unroll 8
+  for (int j = 30; j >= 0; --j) {
+    q = tmin(q, ln[j]);
+    ln[j] = q;
+  }
+  u64 P = KEY_NONE;
+#pragma unroll 8
+  for (int i = 0; i < 31; ++i) {
+    P = tmin(P, ln[32 + i]);
+    ln[i + 1] = tmin(ln[i + 1], P);
+  }
+}
+
+// Argmin-tracking variants for the cell-minimum pass.  Besides the window
+// minimum they record, per output cell, the offset d = cell - anchor of the
+// candidate that achieved it (0 .. K-1), or ARG_NONE when the window has no
+// live candidate.  la is the line's byte buffer (same slots as ln).
+constexpr u8 ARG_NONE = 0xFF;
+
+template <int K>
+__device__ __forceinline__ void line_bwd_arg(u64* ln, u8* la) {
+  constexpr int NB = 32 / K;
+  u64 q[K];
+  int qa[K];  // slot of the suffix minimum, relative to the block start
+  q[0] = KEY_NONE;
+  qa[0] = 0;
+#pragma unroll
+  for (int j = 1; j < K; ++j) { q[j] = ln[32 - K + j]; qa[j] = j; }
+#pragma unroll
+  for (int j = K - 2; j >= 0; --j)
+    if (q[j + 1] < q[j]) { q[j] = q[j + 1]; qa[j] = qa[j + 1]; }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    u64 w[K];
+    int wa[K];
+    u64 P = KEY_NONE;
+    int pa = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const u64 v = ln[32 + b * K + i];
+      if (b + 1 < NB) { w[i] = v; wa[i] = i; }
+      if (v < P) { P = v; pa = i; }
+      u64 out = P;
+      int d = i - pa;
+      if (i + 1 < K && q[(i + 1) % K] < P) {
+        out = q[(i + 1) % K];
+        d = i + K - qa[(i + 1) % K];
+      }
+      ln[32 + b * K + i] = out;
+      la[32 + b * K + i] = out == KEY_NONE ? ARG_NONE : (u8)d;
+    }
+    if (b + 1 < NB) {
+#pragma unroll
+      for (int j = K - 2; j >= 0; --j)
+        if (w[j + 1] < w[j]) { w[j] = w[j + 1]; wa[j] = wa[j + 1]; }
+#pragma unroll
+      for (int j = 0; j < K; ++j) { q[j] = w[j]; qa[j] = wa[j]; }
+    }
+  }
+}
+
+// K = 32: the suffix minima of the previous block stay in the shared line.
+__device__ __forceinline__ void line_bwd32_arg_smem(u64* ln, u8* la) {
+  u64 q = KEY_NONE;
+  int qa = 0;
+#pragma unroll 8
+  for (int j = 31; j >= 1; --j) {
+    const u64 v = ln[j];
+    if (v < q) { q = v; qa = j; }
+    ln[j] = q;
+    la[j] = (u8)qa;
+  }
+  u64 P = KEY_NONE;
+  int pa = 0;
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i) {
+    const u64 v = ln[32 + i];
+    if (v < P) { P = v; pa = i; }
+    u64 out = P;
+    int d = i - pa;
+    if (i < 31) {
+      const u64 qv = ln[i + 1];
+      if (qv < P) { out = qv; d = i + 32 - la[i + 1]; }
+    }
+    ln[32 + i] = out;
+    la[32 + i] = out == KEY_NONE ? ARG_NONE : (u8)d;
+  }
+}
+
 constexpr int LN = 65;  // padded line length (u64) of the tile line buffers
+constexpr int LA = 68;  // line length of the byte buffers (17 words: conflict-free per line)
 
 // Asynchronous global -> shared copies (cp.async): a tile's staging loads are
 // all in flight together instead of one latency per loop iteration.
@@ -117,6 +228,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -172,18 +287,28 @@ __device__ __forceinline__ void accept_warp(const Group& g, u32* occw, u32 T, u3
   }
 }
 
-// Pass 1 of a round.  64 threads per tile, persistent over (sample, tile).
-//  (a) lane-parallel: live priorities of the horizontal candidates anchored
-//      in each tile row (and the K-1 before it) and of the vertical ones of
-//      each tile column, into line buffers lh[row][.], lv[col][.];
+constexpr u32 TILE_THREADS = 128;
+
+// Pass 1 of a round.  128 threads per tile, persistent over (sample, tile):
+// warps 0-1 take the tile's rows (horizontal candidates), warps 2-3 its
+// columns (vertical candidates), 16 lines each.
+//  (a) lane-parallel: live priorities of the candidates anchored on each line
+//      (and the K-1 positions before it) into line buffers lh[row][.],
+//      lv[col][.] (slot 32 + p = position p, p in -32 .. 31);
 //  (b) one thread per line: width-K backward window minima, in place;
 //  (c) cmin(y, x) = min(lh[y][32+x], lv[x][32+y]) written out coalesced.
 template <int K>
-__global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw, u8* dead) {
+__global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc, u32* occw,
+                                                            u8* dead) {
   __shared__ u32 ow[96][3];     // occupancy words: rows Y-32 .. Y+63, word columns wx-1 .. wx+1
-  __shared__ u64 lh[32][LN];    // row lines, positions -32 .. 31
-  __shared__ u64 lv[32][LN];    // column lines, positions -32 .. 31
+  __shared__ u64 lh[32][LN];
+  __shared__ u64 lv[32][LN];
+  __shared__ u32 colmask[32][2];  // occupancy of each tile column: rows Y-32.., rows Y..
+  __shared__ u32 live_sh[2];      // per direction: bit r = line r has a live candidate
+  __shared__ u8 ah[32][LA];       // argmin offsets of the row lines
+  __shared__ u8 av[32][LA];       // argmin offsets of the column lines
   const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 dirw = warp >> 1, half = warp & 1;
   const u32 L = g.L, T = tc.T, T2 = tc.T2;
   for (ItemIter it(blockIdx.x, T2); it.s < g.n; it.next(gridDim.x, T2)) {
     const u32 s = it.s, t = it.t;
@@ -198,25 +323,26 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
       const u32 wc = wrap_lo((int)(tx + c) - 1, T);
       cp_async4(&ow[r][c], owg + (size_t)row * T + wc);
     }
+    if (threadIdx.x < 2) live_sh[threadIdx.x] = 0;
     cp_async_wait_all();
     __syncthreads();
     // splitmix64 input of candidate idx is zb + gamma * idx
     const u64 zb = g.base[s] + SM_GAMMA;
     const bool caller = g.keys != nullptr;
-    u64 (*ln)[LN] = warp == 0 ? lh : lv;
-    u32 live = 0;          // bit r: line r has a live candidate (warp-uniform)
-    u32 keyed = 0;         // live candidates given a key (warp-uniform)
+    u64 (*ln)[LN] = dirw == 0 ? lh : lv;
+    u32 live = 0;    // lines of this warp with a live candidate (warp-uniform)
+    u32 keyed = 0;   // live candidates this lane gave a key
+    const u32 l0 = half * 16;
     if (K >= 16) {
       // long windows: the K-1 positions before the tile are hashed in the
-      // same pass as the tile's own, lane = position (slot lane = position
-      // lane - 32, slot 32 + lane = position lane)
+      // same pass as the tile's own, lane = position
       const bool need_prev = lane >= 33u - K;
-      if (warp == 0) {
+      if (dirw == 0) {
         const u64 zstep = SM_GAMMA * (u64)L;
-        u64 zc = zb + SM_GAMMA * ((u64)Y * L + X + lane);
-        u64 zp = zb + SM_GAMMA * ((u64)Y * L + wrap_lo((int)(X + lane) - 32, L));
+        u64 zc = zb + SM_GAMMA * ((u64)(Y + l0) * L + X + lane);
+        u64 zp = zb + SM_GAMMA * ((u64)(Y + l0) * L + wrap_lo((int)(X + lane) - 32, L));
 #pragma unroll 2
-        for (u32 r = 0; r < 32; ++r, zc += zstep, zp += zstep) {
+        for (u32 r = l0; r < l0 + 16; ++r, zc += zstep, zp += zstep) {
           const u64 A = ((u64)ow[32 + r][1] << 32) | ow[32 + r][0];  // positions -32 .. 31
           const u64 B = ((u64)ow[32 + r][2] << 32) | ow[32 + r][1];  // positions 0 .. 63
           const bool ap = need_prev && ((A >> lane) & kmask<K>()) == 0;
@@ -234,7 +360,7 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             vp = ap ? hp : KEY_NONE;
             vc = ac ? hc : KEY_NONE;
             live |= 1u << r;
-            keyed += __popc(__ballot_sync(FULL, ap)) + __popc(__ballot_sync(FULL, ac));
+            keyed += (u32)ap + (u32)ac;
           }
           lh[r][lane] = vp;
           lh[r][32 + lane] = vc;
@@ -243,9 +369,9 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
         const u32 bp = ow[lane][1], bc = ow[32 + lane][1], bn = ow[64 + lane][1];
         const u64 rowp = g.LL + (u64)wrap_lo((int)(Y + lane) - 32, L) * L + X;
         const u64 rowc = g.LL + (u64)(Y + lane) * L + X;
-        u64 zc = zb + SM_GAMMA * rowc, zp = zb + SM_GAMMA * rowp;
+        u64 zc = zb + SM_GAMMA * (rowc + l0), zp = zb + SM_GAMMA * (rowp + l0);
 #pragma unroll 2
-        for (u32 c = 0; c < 32; ++c, zc += SM_GAMMA, zp += SM_GAMMA) {
+        for (u32 c = l0; c < l0 + 16; ++c, zc += SM_GAMMA, zp += SM_GAMMA) {
           const u32 Mp = __ballot_sync(FULL, (bp >> c) & 1u);
           const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
           const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
@@ -265,20 +391,21 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             vp = ap ? hp : KEY_NONE;
             vc = ac ? hc : KEY_NONE;
             live |= 1u << c;
-            keyed += __popc(__ballot_sync(FULL, ap)) + __popc(__ballot_sync(FULL, ac));
+            keyed += (u32)ap + (u32)ac;
           }
           lv[c][lane] = vp;
           lv[c][32 + lane] = vc;
         }
       }
+      if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
+      __syncthreads();
     } else {
-      u32 cp = 0, cc = 0;    // vertical warp: occupancy of column `lane`, rows Y-32.. / Y..
-      if (warp == 0) {
+      if (dirw == 0) {
         // tile part of each row, lane = position along the row
-        u64 z = zb + SM_GAMMA * ((u64)Y * L + X + lane);
+        u64 z = zb + SM_GAMMA * ((u64)(Y + l0) * L + X + lane);
         const u64 zstep = SM_GAMMA * (u64)L;
 #pragma unroll 2
-        for (u32 r = 0; r < 32; ++r, z += zstep) {
+        for (u32 r = l0; r < l0 + 16; ++r, z += zstep) {
           const u64 B = ((u64)ow[32 + r][2] << 32) | ow[32 + r][1];  // positions 0 .. 63
           const bool ac = ((B >> lane) & kmask<K>()) == 0;
           const u32 m = __ballot_sync(FULL, ac);
@@ -287,20 +414,20 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             const u64 h = caller ? g.keys[(u64)(Y + r) * L + X + lane] : mix64(z);
             vc = ac ? h : KEY_NONE;
             live |= 1u << r;
-            keyed += __popc(m);
+            keyed += (u32)ac;
           }
           lh[r][32 + lane] = vc;
         }
       } else {
         // tile part of each column, lane = position along the column
         const u32 bp = ow[lane][1], bc = ow[32 + lane][1], bn = ow[64 + lane][1];
-        u64 z = zb + SM_GAMMA * (g.LL + (u64)(Y + lane) * L + X);
+        u64 z = zb + SM_GAMMA * (g.LL + (u64)(Y + lane) * L + X + l0);
 #pragma unroll 2
-        for (u32 c = 0; c < 32; ++c, z += SM_GAMMA) {
+        for (u32 c = l0; c < l0 + 16; ++c, z += SM_GAMMA) {
           const u32 Mp = __ballot_sync(FULL, (bp >> c) & 1u);
           const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
           const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
-          if (lane == c) { cp = Mp; cc = Mc; }
+          if (lane == 0) { colmask[c][0] = Mp; colmask[c][1] = Mc; }
           const u64 B = ((u64)Mn << 32) | Mc;
           const bool ac = ((B >> lane) & kmask<K>()) == 0;
           const u32 m = __ballot_sync(FULL, ac);
@@ -309,60 +436,75 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
             const u64 h = caller ? g.keys[g.LL + (u64)(Y + lane) * L + X + c] : mix64(z);
             vc = ac ? h : KEY_NONE;
             live |= 1u << c;
-            keyed += __popc(m);
+            keyed += (u32)ac;
           }
           lv[c][32 + lane] = vc;
         }
       }
+      __syncthreads();  // colmask complete
       // short windows: the K-1 positions before the tile on every line,
-      // packed densely over lanes: item f = i*32 + lane is line f / (K-1),
-      // position -(K-1) + f % (K-1)
+      // packed densely over lanes (item f = i*32 + lane is line f / (K-1),
+      // position -(K-1) + f % (K-1)); the two warps of a direction split
+      // the K-1 rounds of items
       constexpr u32 KP = K > 1 ? K - 1 : 1;
 #pragma unroll 1
-      for (u32 i = 0; i + 1 < (u32)K; ++i) {
+      for (u32 i = half; i + 1 < (u32)K; i += 2) {
         const u32 f = i * 32 + lane, line = f / KP, j = f - line * KP;
         const int pos = (int)j - (int)KP;
-        u64 A;
-        if (warp == 0) {
-          A = ((u64)ow[32 + line][1] << 32) | ow[32 + line][0];  // positions -32 .. 31
-        } else {
-          const u32 lp = __shfl_sync(FULL, cp, line), lc = __shfl_sync(FULL, cc, line);
-          A = ((u64)lc << 32) | lp;
-        }
+        const u64 A = dirw == 0 ? (((u64)ow[32 + line][1] << 32) | ow[32 + line][0])
+                                : (((u64)colmask[line][1] << 32) | colmask[line][0]);
         const bool ap = ((A >> (pos + 32)) & kmask<K>()) == 0;
-        const u64 idx = warp == 0 ? (u64)(Y + line) * L + wrap_lo((int)X + pos, L)
+        const u64 idx = dirw == 0 ? (u64)(Y + line) * L + wrap_lo((int)X + pos, L)
                                   : g.LL + (u64)wrap_lo((int)Y + pos, L) * L + X + line;
         u64 v = KEY_NONE;
         if (__any_sync(FULL, ap)) {
           const u64 h = caller ? g.keys[idx] : mix64(zb + SM_GAMMA * idx);
           v = ap ? h : KEY_NONE;
+          keyed += (u32)ap;
         }
         ln[line][32 + pos] = v;
         live |= __reduce_or_sync(FULL, ap ? 1u << line : 0u);
-        keyed += __popc(__ballot_sync(FULL, ap));
       }
+      if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
+      __syncthreads();
     }
-    __syncthreads();
-    {
-      u64* mine_ln = ln[lane];
-      if ((live >> lane) & 1u) {
-        line_bwd<K>(mine_ln);
+    if (threadIdx.x < 64) {
+      const u32 d = threadIdx.x >> 5;
+      u64* mine_ln = (d == 0 ? lh : lv)[lane];
+      u8* mine_la = (d == 0 ? ah : av)[lane];
+      if ((live_sh[d] >> lane) & 1u) {
+        if (K == 32) line_bwd32_arg_smem(mine_ln, mine_la);
+        else line_bwd_arg<K>(mine_ln, mine_la);
       } else {
 #pragma unroll 8
-        for (int x = 0; x < 32; ++x) mine_ln[32 + x] = KEY_NONE;
+        for (int x = 0; x < 32; ++x) {
+          mine_ln[32 + x] = KEY_NONE;
+          mine_la[32 + x] = ARG_NONE;
+        }
       }
     }
     __syncthreads();
+    // argmin code of every cell: offset d of the winning horizontal
+    // candidate (0 .. K-1), 32 + d for a vertical one, ARG_NONE if no live
+    // candidate covers the cell; 8 cells per thread, one 8-byte store
     bool any = false;
-    u64* cmg = g.cmin + (size_t)s * g.LL;
-#pragma unroll 4
-    for (u32 i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-      const u32 y = i >> 5, c = i & 31;
-      const u64 v = tmin(lh[y][32 + c], lv[c][32 + y]);
-      cmg[(size_t)(Y + y) * L + X + c] = v;
-      any |= v != KEY_NONE;
+    u8* cdg = reinterpret_cast<u8*>(g.cmin) + (size_t)s * g.LL;
+    {
+      const u32 y = threadIdx.x >> 2, c0 = (threadIdx.x & 3) * 8;
+      u64 pack = 0;
+#pragma unroll
+      for (u32 c = c0; c < c0 + 8; ++c) {
+        const u64 vh = lh[y][32 + c], vv = lv[c][32 + y];
+        u32 code = ARG_NONE;
+        if (vh < vv) code = ah[y][32 + c];
+        else if (vv < vh) code = 32u + av[c][32 + y];
+        pack |= (u64)code << (8 * (c - c0));
+        any |= code != ARG_NONE;
+      }
+      *reinterpret_cast<u64*>(cdg + (size_t)(Y + y) * L + X + c0) = pack;
     }
     const bool tile_live = __syncthreads_or(any);
+    keyed = __reduce_add_sync(FULL, keyed);
     if (lane == 0 && keyed) atomicAdd(g.work + 1, (u64)keyed);
     if (threadIdx.x == 0) {
       atomicAdd(g.work + 0, 1024ull);
@@ -373,18 +515,22 @@ __global__ void __launch_bounds__(64) k_tile_cmin(Group g, TileCfg tc, u32* occw
 }
 
 // Pass 2 of a round: acceptance of candidates anchored in each live tile.
-//  (a) stage cmin: row lines (own tile + the tile to the right) and column
-//      lines (own tile + the tile below); a dead neighbour reads as "none";
-//  (b) one thread per line: width-K forward window minima, in place;
-//  (c) lane-parallel: a live candidate whose window minimum equals its key
-//      is accepted; accepted candidates are written by the whole warp.
+// A live candidate has the smallest key on all of its cells iff each of its
+// cells carries its argmin code: a horizontal candidate at x is accepted iff
+// code(x + i) = i for i < K, a vertical one iff code(y + i) = 32 + i.  With
+// S = "code is the start value" and INC = "the next cell's code is this
+// code + 1" as bit masks along a line (ballots), that is S(x) and
+// INC(x .. x+K-2).  No priority is needed except for the accepted ones.
+//  (a) stage the codes of the tile, the tile to the right (rows) and the
+//      tile below (columns); a dead neighbour reads as ARG_NONE;
+//  (b) warps 0-1 take 16 rows each, warps 2-3 16 columns each.
 template <int K>
-__global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* occw,
-                                                    const u8* dead) {
-  __shared__ u32 ow[64][2];     // occupancy words rows Y .. Y+63, word columns wx, wx+1
-  __shared__ u64 lh[32][LN];    // row lines: columns X .. X+63
-  __shared__ u64 lv[32][LN];    // column lines: rows Y .. Y+63
+__global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg tc, u32* occw,
+                                                              const u8* dead) {
+  __shared__ __align__(16) u8 hc[32][80];   // row y: codes of columns X .. X+63 (+ slack)
+  __shared__ __align__(16) u8 vc[65][36];   // row j: codes of rows Y .. Y+63, columns X .. X+31
   const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 dirw = warp >> 1, half = warp & 1;
   const u32 L = g.L, T = tc.T, T2 = tc.T2;
   for (ItemIter it(blockIdx.x, T2); it.s < g.n; it.next(gridDim.x, T2)) {
     const u32 s = it.s, t = it.t;
@@ -394,76 +540,69 @@ __global__ void __launch_bounds__(64) k_tile_accept(Group g, TileCfg tc, u32* oc
     const u32 ty = t / T, tx = t - ty * T, Y = ty * 32, X = tx * 32;
     const u32 txr = tx + 1 == T ? 0 : tx + 1, tyb = ty + 1 == T ? 0 : ty + 1;
     const bool dr = dflag[ty * T + txr] != 0, db = dflag[tyb * T + tx] != 0;
-    const u64* cmg = g.cmin + (size_t)s * g.LL;
-    const u32* owg = occw + (size_t)s * L * T;
-    for (u32 i = threadIdx.x; i < 64 * 2; i += blockDim.x) {
-      const u32 r = i >> 1, c = i & 1;
-      cp_async4(&ow[r][c], owg + (size_t)wrap_lo((int)(Y + r), L) * T + (c ? txr : tx));
+    const u8* cdg = reinterpret_cast<const u8*>(g.cmin) + (size_t)s * g.LL;
+    // row lines: 16-byte chunks of the own tile and the tile to the right
+    for (u32 i = threadIdx.x; i < 128; i += blockDim.x) {
+      const u32 part = i >> 6, r = (i >> 1) & 31, hlf = i & 1;
+      u8* dst = &hc[r][part * 32 + hlf * 16];
+      if (part == 1 && dr)
+        *reinterpret_cast<uint4*>(dst) = make_uint4(~0u, ~0u, ~0u, ~0u);
+      else
+        cp_async16(dst, cdg + (size_t)(Y + r) * L + (part ? txr * 32 : X) + hlf * 16);
     }
-#pragma unroll 4
-    for (u32 i = threadIdx.x; i < 32 * 32; i += blockDim.x) {
-      const u32 r = i >> 5, c = i & 31;
-      const u64* own = cmg + (size_t)(Y + r) * L + X + c;
-      cp_async8(&lh[r][c], own);
-      cp_async8(&lv[c][r], own);
-      if (dr) lh[r][32 + c] = KEY_NONE;
-      else cp_async8(&lh[r][32 + c], cmg + (size_t)(Y + r) * L + txr * 32 + c);
-      if (db) lv[c][32 + r] = KEY_NONE;
-      else cp_async8(&lv[c][32 + r], cmg + (size_t)(tyb * 32 + r) * L + X + c);
+    // column lines (rows of the own tile and the tile below): 4-byte words
+    // into a 36-byte row pitch, which keeps the per-column reads conflict-free
+    for (u32 i = threadIdx.x; i < 512; i += blockDim.x) {
+      const u32 r = i >> 3, wd = i & 7;
+      u8* dst = &vc[r][wd * 4];
+      if (r >= 32 && db)
+        *reinterpret_cast<u32*>(dst) = ~0u;
+      else
+        cp_async4(dst, cdg + (size_t)(r < 32 ? Y + r : tyb * 32 + r - 32) * L + X + wd * 4);
+    }
+    if (threadIdx.x < 32) {
+      hc[threadIdx.x][64] = ARG_NONE;
+      vc[64][threadIdx.x] = ARG_NONE;
     }
     cp_async_wait_all();
     __syncthreads();
-    if (warp == 0) line_fwd<K>(lh[lane]);
-    else line_fwd<K>(lv[lane]);
-    __syncthreads();
     const u64 zb = g.base[s] + SM_GAMMA;
     const bool caller = g.keys != nullptr;
-    u32 keyed = 0;
-    if (warp == 0) {
-      u64 z = zb + SM_GAMMA * ((u64)Y * L + X + lane);
-      const u64 zstep = SM_GAMMA * (u64)L;
-#pragma unroll 2
-      for (u32 r = 0; r < 32; ++r, z += zstep) {
-        const u64 f = lh[r][lane];
-        const u64 B = ((u64)ow[r][1] << 32) | ow[r][0];
-        const bool cand = f != KEY_NONE && ((B >> lane) & kmask<K>()) == 0;
-        if (__any_sync(FULL, cand)) {
-          const u64 idx = (u64)(Y + r) * L + X + lane;
-          const u64 key = caller ? g.keys[idx] : mix64(z);
-          keyed += __popc(__ballot_sync(FULL, cand));
-          u32 m = __ballot_sync(FULL, cand && f == key);
-          while (m) {
-            const u32 src = __ffs(m) - 1;
-            m &= m - 1;
-            accept_warp(g, occw, T, s, (u32)__shfl_sync(FULL, idx, src), __shfl_sync(FULL, f, src));
-          }
-        }
+    constexpr u64 KM1 = K > 1 ? ((1ull << (K - 1)) - 1ull) : 0ull;  // INC bits a window needs
+    const u32 l0 = half * 16;
+    u32 accepted = 0;
+    for (u32 line = l0; line < l0 + 16; ++line) {
+      u32 c0, c1, c2, c3;
+      if (dirw == 0) {
+        c0 = hc[line][lane];
+        c1 = hc[line][lane + 1];
+        c2 = hc[line][32 + lane];
+        c3 = hc[line][33 + lane];
+      } else {
+        c0 = vc[lane][line];
+        c1 = vc[lane + 1][line];
+        c2 = vc[32 + lane][line];
+        c3 = vc[33 + lane][line];
       }
-    } else {
-      const u32 bc = ow[lane][0], bn = ow[32 + lane][0];
-      const u64 rowc = g.LL + (u64)(Y + lane) * L + X;
-      u64 z = zb + SM_GAMMA * rowc;
-#pragma unroll 2
-      for (u32 c = 0; c < 32; ++c, z += SM_GAMMA) {
-        const u32 Mc = __ballot_sync(FULL, (bc >> c) & 1u);
-        const u32 Mn = __ballot_sync(FULL, (bn >> c) & 1u);
-        const u64 B = ((u64)Mn << 32) | Mc;
-        const u64 f = lv[c][lane];
-        const bool cand = f != KEY_NONE && ((B >> lane) & kmask<K>()) == 0;
-        if (__any_sync(FULL, cand)) {
-          const u64 idx = rowc + c;
-          const u64 key = caller ? g.keys[idx] : mix64(z);
-          keyed += __popc(__ballot_sync(FULL, cand));
-          u32 m = __ballot_sync(FULL, cand && f == key);
-          while (m) {
-            const u32 src = __ffs(m) - 1;
-            m &= m - 1;
-            accept_warp(g, occw, T, s, (u32)__shfl_sync(FULL, idx, src), __shfl_sync(FULL, f, src));
-          }
-        }
+      const u32 base = dirw == 0 ? 0u : 32u;   // code of offset 0
+      const u32 top = base + 31u;
+      const u32 S = __ballot_sync(FULL, c0 == base);
+      if (!S) continue;
+      const u64 inc = (u64)__ballot_sync(FULL, c0 >= base && c0 < top && c1 == c0 + 1) |
+                      ((u64)__ballot_sync(FULL, c2 >= base && c2 < top && c3 == c2 + 1) << 32);
+      const bool acc = ((S >> lane) & 1u) && ((inc >> lane) & KM1) == KM1;
+      u32 m = __ballot_sync(FULL, acc);
+      while (m) {
+        const u32 src = __ffs(m) - 1;
+        m &= m - 1;
+        const u64 idx = dirw == 0 ? (u64)(Y + line) * L + X + src
+                                  : g.LL + (u64)(Y + src) * L + X + line;
+        const u64 key = caller ? g.keys[idx] : mix64(zb + SM_GAMMA * idx);
+        accept_warp(g, occw, T, s, (u32)idx, key);
+        ++accepted;
       }
     }
-    if (lane == 0 && keyed) atomicAdd(g.work + 3, (u64)keyed);
+    if (lane == 0 && accepted) atomicAdd(g.work + 3, (u64)accepted);
     if (threadIdx.x == 0) atomicAdd(g.work + 2, 1024ull);
     __syncthreads();
   }
