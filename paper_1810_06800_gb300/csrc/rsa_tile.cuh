@@ -468,13 +468,42 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
       if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
       __syncthreads();
     }
-    if (threadIdx.x < 64) {
+    if (K == 32) {
+      // K = 32: every output window = suffix of the previous block + prefix
+      // of the tile's block; threads 0-63 build the suffix minima Q (slots
+      // 1..31), threads 64-127 the prefix minima P (slots 32..63) of the
+      // same 64 lines, in place with their argmin slots; the write-out below
+      // takes min(Q[x+1], P[x])
+      const u32 ln_id = threadIdx.x & 63;
+      u64* mine_ln = (ln_id < 32 ? lh : lv)[ln_id & 31];
+      u8* mine_la = (ln_id < 32 ? ah : av)[ln_id & 31];
+      if (threadIdx.x < 64) {
+        u64 q = KEY_NONE;
+        int qa = 0;
+#pragma unroll 8
+        for (int j = 31; j >= 1; --j) {
+          const u64 v = mine_ln[j];
+          if (v < q) { q = v; qa = j; }
+          mine_ln[j] = q;
+          mine_la[j] = (u8)qa;
+        }
+      } else {
+        u64 P = KEY_NONE;
+        int pa = 0;
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) {
+          const u64 v = mine_ln[32 + i];
+          if (v < P) { P = v; pa = i; }
+          mine_ln[32 + i] = P;
+          mine_la[32 + i] = (u8)pa;
+        }
+      }
+    } else if (threadIdx.x < 64) {
       const u32 d = threadIdx.x >> 5;
       u64* mine_ln = (d == 0 ? lh : lv)[lane];
       u8* mine_la = (d == 0 ? ah : av)[lane];
       if ((live_sh[d] >> lane) & 1u) {
-        if (K == 32) line_bwd32_arg_smem(mine_ln, mine_la);
-        else line_bwd_arg<K>(mine_ln, mine_la);
+        line_bwd_arg<K>(mine_ln, mine_la);
       } else {
 #pragma unroll 8
         for (int x = 0; x < 32; ++x) {
@@ -494,10 +523,27 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
       u64 pack = 0;
 #pragma unroll
       for (u32 c = c0; c < c0 + 8; ++c) {
-        const u64 vh = lh[y][32 + c], vv = lv[c][32 + y];
+        u64 vh = lh[y][32 + c], vv = lv[c][32 + y];
+        u32 dh, dv;
+        if (K == 32) {
+          // window of cell c on row y: Q[c+1] (previous block) vs P[c]
+          dh = c - ah[y][32 + c];
+          if (c < 31) {
+            const u64 q = lh[y][c + 1];
+            if (q < vh) { vh = q; dh = c + 32 - ah[y][c + 1]; }
+          }
+          dv = y - av[c][32 + y];
+          if (y < 31) {
+            const u64 q = lv[c][y + 1];
+            if (q < vv) { vv = q; dv = y + 32 - av[c][y + 1]; }
+          }
+        } else {
+          dh = ah[y][32 + c];
+          dv = av[c][32 + y];
+        }
         u32 code = ARG_NONE;
-        if (vh < vv) code = ah[y][32 + c];
-        else if (vv < vh) code = 32u + av[c][32 + y];
+        if (vh < vv) code = dh;
+        else if (vv < vh) code = 32u + dv;
         pack |= (u64)code << (8 * (c - c0));
         any |= code != ARG_NONE;
       }
