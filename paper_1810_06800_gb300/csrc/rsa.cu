@@ -48,7 +48,7 @@ constexpr size_t SMEM_BUDGET = 160 * 1024;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t occ, occw, occT, cB, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
+  size_t occ, occw, occT, cB, code16, code16T, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
       ebkt, nkey_b, nbkt, st, seeds, counters, keys,
       scratch, total;
 };
@@ -57,7 +57,7 @@ struct Geometry {
   bool tile;                    // power-of-two k <= 32 and L % 32 == 0
   bool line;                    // 32 <= k <= LINE_KMAX, L % 32 == 0, not tile
   LineCfg lc;
-  size_t line_smem;
+  size_t line_smem, line_codes_smem;
   TileCfg tc;                   // (items filled per run)
   RowCfg row;
   ColCfg col;
@@ -92,6 +92,7 @@ Geometry plan(u32 L, u32 k) {
     G.lc.nmax = S + k - 1;
     G.lc.T = L / 32;
     G.line_smem = line_smem_bytes(G.lc.nmax, S, k);
+    G.line_codes_smem = line_codes_smem_bytes(G.lc.nmax);
   }
   // ---- row pass: one warp per (row, segment) ----
   RowCfg& r = G.row;
@@ -164,6 +165,8 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   l.occw = take(bits ? n * LL / 8 : 0);
   l.occT = take(G.line ? n * LL / 8 : 0);
   l.cB = take(G.line ? n * LL * 8 : 0);
+  l.code16 = take(G.line ? n * LL * 2 : 0);
+  l.code16T = take(G.line ? n * LL * 2 : 0);
   l.dead = take(G.tile ? (size_t)n * G.tc.T2 : 0);
   l.owner = take(n * LL * 4);
   l.cmin = take(n * LL * (G.tile ? 1 : 8));  // tile path: one argmin code byte per cell
@@ -491,6 +494,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
     if ((rc = set_smem(k_line_cmin<1>, G.line_smem))) return rc;
     if ((rc = set_smem(k_line_accept<0>, G.line_smem))) return rc;
     if ((rc = set_smem(k_line_accept<1>, G.line_smem))) return rc;
+    if ((rc = set_smem(k_line_accept_codes<0>, G.line_codes_smem))) return rc;
+    if ((rc = set_smem(k_line_accept_codes<1>, G.line_codes_smem))) return rc;
   } else if (!G.tile) {
     if ((rc = set_smem(k_row<0>, G.row_smem))) return rc;
     if ((rc = set_smem(k_row<1>, G.row_smem))) return rc;
@@ -527,11 +532,23 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
                G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
         launch(h, KD_LINE_CMIN_V, k_line_cmin<1>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
                G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
-        launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, st, g, g.cmin, cB);
-        launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
-               G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
-        launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
-               G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
+        if (h->with_keys) {
+          // caller-supplied priorities cannot be inverted: compare values
+          launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, st, g, g.cmin, cB);
+          launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_smem, st,
+                 g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
+          launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_smem, st,
+                 g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
+        } else {
+          u16* c16 = reinterpret_cast<u16*>(b + l.code16);
+          u16* c16T = reinterpret_cast<u16*>(b + l.code16T);
+          launch(h, KD_LINE_COMBINE, k_line_codes, tg, dim3(256), 0, st, g, (const u64*)g.cmin,
+                 (const u64*)cB, c16, c16T);
+          launch(h, KD_LINE_ACCEPT_H, k_line_accept_codes<0>, lg, dim3(LINE_THREADS),
+                 G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T);
+          launch(h, KD_LINE_ACCEPT_V, k_line_accept_codes<1>, lg, dim3(LINE_THREADS),
+                 G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T);
+        }
       } else {
         launch(h, KD_ROW_CMIN, k_row<0>, rg, dim3(G.row_threads), G.row_smem, st, g, G.row);
         launch(h, KD_COL_CMIN, k_col<0>, cg, dim3(G.col_threads), G.col_smem, st, g, G.col);

@@ -51,6 +51,18 @@ __device__ __forceinline__ u64 mix64(u64 z) {
   return z ^ (z >> 31);
 }
 
+// Inverse of mix64: each xor-shift z ^ (z >> s) is undone by xoring the
+// shifts s, 2s, ... below 64, each odd multiplier by its inverse mod 2^64.
+__device__ __forceinline__ u64 mix64_inverse(u64 z) {
+  z = z ^ (z >> 31) ^ (z >> 62);
+  z *= 0x319642B2D24D8EC3ull;  // inverse of 0x94D049BB133111EB
+  z = z ^ (z >> 27) ^ (z >> 54);
+  z *= 0x96DE1B173F119089ull;  // inverse of 0xBF58476D1CE4E5B9
+  z = z ^ (z >> 30) ^ (z >> 60);
+  return z;
+}
+constexpr u64 SM_GAMMA_INV = 0xF1DE83E19937733Dull;  // inverse of the golden gamma
+
 struct Edge {          // one contact between two k-mers (24 bytes)
   u64 time;            // max of the two k-mers' priorities
   u32 m1, m2;          // node ids (acceptance order)

@@ -269,6 +269,57 @@ __global__ void __launch_bounds__(256) k_line_combine(Group g, u64* cA, u64* cB)
   }
 }
 
+// Seeded priorities only: cmin of each cell as a 2-byte argmin code, in both
+// layouts.  The winning key is inverted (mix64 is a bijection) back to its
+// candidate idx, whose anchor gives the offset d = cell - anchor along the
+// line: code d (0 .. k-1) for a horizontal winner, 0x8000 | d for a vertical
+// one, CODE_NONE when no live candidate covers the cell.
+constexpr u16 CODE_NONE = 0xFFFF;
+constexpr u16 CODE_V = 0x8000;
+
+__global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, const u64* cB,
+                                                    u16* code, u16* codeT) {
+  __shared__ u16 tc[32][34];
+  const u32 s = blockIdx.y;
+  if (g.st[s].done) return;
+  const u32 L = g.L, T = L / 32;
+  const u32 ty = blockIdx.x / T, tx = blockIdx.x % T;
+  const u64* A = cA + (size_t)s * g.LL;
+  const u64* B = cB + (size_t)s * g.LL;
+  u16* C = code + (size_t)s * g.LL;
+  u16* CT = codeT + (size_t)s * g.LL;
+  const u64 zb = g.base[s] + SM_GAMMA;
+  for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
+    const u32 r = i >> 5, c = i & 31;                 // cell (y, x) = (ty*32 + r, tx*32 + c)
+    const u32 y = ty * 32 + r, x = tx * 32 + c;
+    const u64 vh = A[(size_t)y * L + x];
+    const u64 vv = B[(size_t)x * L + y];
+    u16 out = CODE_NONE;
+    if (vh != vv) {
+      const u64 m = vh < vv ? vh : vv;
+      const u32 idx = (u32)((mix64_inverse(m) - zb) * SM_GAMMA_INV);
+      if (vh < vv) {
+        const u32 xa = (idx / L) * L;            // row start of the anchor
+        u32 d = x + L - (idx - xa);
+        if (d >= L) d -= L;
+        out = (u16)d;
+      } else {
+        const u32 ya = (idx - (u32)g.LL) / L;
+        u32 d = y + L - ya;
+        if (d >= L) d -= L;
+        out = (u16)(CODE_V | d);
+      }
+    }
+    C[(size_t)y * L + x] = out;
+    tc[r][c] = out;
+  }
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
+    const u32 r = i >> 5, c = i & 31;                 // row x = tx*32 + r of the transpose
+    CT[(size_t)(tx * 32 + r) * L + ty * 32 + c] = tc[c][r];
+  }
+}
+
 // Record an accepted candidate with the whole block: node, occupancy bits in
 // both layouts, owner ids of its k cells.
 __device__ void accept_block(const Group& g, u32* occw, u32* occT, u32 T, u32 s, u32 idx, u64 key,
@@ -364,6 +415,89 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_accept(Group g, LineCfg l
     accept_block(g, occw, occT, T, s, (u32)idx, key, &node_sh);
   }
   if (na > LINE_ACC && threadIdx.x == 0) atomicOr(&g.st[s].status, ST_NODE_OVF);
+}
+
+// Acceptance from argmin codes (seeded priorities): along a line (F = 0 a row
+// of code, F = 1 a row of codeT), the candidate anchored at position v is
+// accepted iff code(v) = base and code(j + 1) = code(j) + 1 for the k-1
+// steps j = v .. v+k-2.  "Breaks" of that pattern are packed into words by
+// warp ballots; a popcount prefix answers each anchor with two lookups.
+template <int F>
+__global__ void __launch_bounds__(LINE_THREADS) k_line_accept_codes(Group g, LineCfg lc,
+                                                                    u32* occw, u32* occT,
+                                                                    const u16* code,
+                                                                    const u16* codeT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const u32 s = blockIdx.y;
+  if (g.st[s].done) return;
+  const u32 L = g.L, k = g.k, T = lc.T;
+  const u32 line = blockIdx.x / lc.nseg, seg = blockIdx.x % lc.nseg;
+  const u32 x0 = seg * lc.S;
+  const u32 Se = min(lc.S, L - x0);
+  const u32 n = Se + k - 1;                  // codes x0 .. x0+n-1
+  const u32 nwords = (n + 31) / 32;
+  u16* cv = reinterpret_cast<u16*>(smem_raw);                 // n (+1) codes
+  u32* brk = reinterpret_cast<u32*>(cv + ((lc.nmax + 2 + 1) & ~1u));
+  u32* pre = brk + ((lc.nmax + 31) / 32 + 2);
+  u32* scr = pre + ((lc.nmax + 31) / 32 + 2);
+  __shared__ u32 nacc, node_sh;
+  __shared__ u32 acc[LINE_ACC];
+  const u16* row = (F == 0 ? code : codeT) + ((size_t)s * L + line) * L;
+  for (u32 u = threadIdx.x; u <= n; u += blockDim.x) {
+    u32 p = x0 + u;
+    while (p >= L) p -= L;
+    cv[u] = row[p];
+  }
+  if (threadIdx.x == 0) nacc = 0;
+  __syncthreads();
+  const u32 base = F == 0 ? 0u : (u32)CODE_V;
+  // break bit of step j (code(j) -> code(j+1)); all threads of a warp walk
+  // the same 32-position words
+  for (u32 w0 = (threadIdx.x >> 5) * 32; w0 < nwords * 32; w0 += blockDim.x) {
+    const u32 j = w0 + (threadIdx.x & 31);
+    bool b = true;
+    if (j < n) {
+      const u32 a = cv[j], c = cv[j + 1];
+      b = !(a >= base && a + 1 < base + k && c == a + 1);
+    }
+    const u32 m = __ballot_sync(FULL, b);
+    if ((threadIdx.x & 31) == 0) brk[w0 >> 5] = m;
+  }
+  __syncthreads();
+  // exclusive popcount prefix of the break words
+  const u32 nch = (nwords + 31) / 32;
+  for (u32 c = threadIdx.x; c < nch; c += blockDim.x) {
+    u32 a = 0;
+    for (u32 i = c * 32; i < min(nwords, c * 32 + 32); ++i) { pre[i] = a; a += __popc(brk[i]); }
+    scr[c] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u32 a = 0;
+    for (u32 c = 0; c < nch; ++c) { const u32 t = scr[c]; scr[c] = a; a += t; }
+  }
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < nwords; i += blockDim.x) pre[i] += scr[i >> 5];
+  __syncthreads();
+  const u64 zb = g.base[s] + SM_GAMMA;
+  for (u32 v = threadIdx.x; v < Se; v += blockDim.x) {
+    if (cv[v] != base) continue;
+    if (k > 1 && bits_before(brk, pre, v + k - 1) != bits_before(brk, pre, v)) continue;
+    const u32 slot = atomicAdd(&nacc, 1u);
+    if (slot < LINE_ACC) acc[slot] = v;
+  }
+  __syncthreads();
+  const u32 na = nacc;
+  for (u32 i = 0; i < na && i < LINE_ACC; ++i) {
+    const u32 pos = x0 + acc[i];
+    const u64 idx = F == 0 ? (u64)line * L + pos : g.LL + (u64)pos * L + line;
+    accept_block(g, occw, occT, T, s, (u32)idx, mix64(zb + SM_GAMMA * idx), &node_sh);
+  }
+  if (na > LINE_ACC && threadIdx.x == 0) atomicOr(&g.st[s].status, ST_NODE_OVF);
+}
+
+__host__ __device__ inline size_t line_codes_smem_bytes(u32 nmax) {
+  return (size_t)((nmax + 2 + 1) & ~1u) * 2 + (size_t)((nmax + 31) / 32 + 2) * 8 + 64 * 4;
 }
 
 }  // namespace rsak
