@@ -13,6 +13,9 @@ What it computes (arXiv:1810.06800):
     in one or both directions (Sec. II.C, II.D), by union-find over k-mers
     with displacement vectors and an exact "disagreeing lift" rule  -> n_c.
     The paper's own |x1-x2|+|y1-y2| > 2k test is evaluated alongside.
+  * The configuration of the first m accepted k-mers: its cluster-size
+    histogram (Sec. II.A Eq. CSD, Sec. III) and the directions in which its
+    clusters wind round the torus  -> :func:`configuration`.
 
 The C code lives in ``rsa_oracle.c``; :func:`build` compiles it with gcc.
 The brute-force checkers in :mod:`oracle.brute` are independent pure-Python
@@ -74,6 +77,9 @@ def _load():
     lib.oracle_is_jammed.argtypes = [u32, u32, vp]
     lib.oracle_contacts.restype = ctypes.c_int
     lib.oracle_contacts.argtypes = [u32, u32, vp, ctypes.c_int64, i64p, i64p, i64p]
+    lib.oracle_configuration.restype = ctypes.c_int
+    lib.oracle_configuration.argtypes = [u32, u32, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int32)]
     lib.oracle_max_free_runs.restype = None
     lib.oracle_max_free_runs.argtypes = [u32, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     _lib = lib
@@ -168,6 +174,23 @@ def contacts(L: int, k: int, accepted):
     if rc != 0:
         raise MemoryError("oracle_contacts failed")
     return int(a.value), int(b.value), int(c.value)
+
+
+def configuration(L: int, k: int, accepted, m: int):
+    """The first m accepted k-mers (scan order) as a configuration
+    (Sec. II.C, II.D): (counts, wrap_x, wrap_y) where counts[s] is the number
+    of clusters of exactly s k-mers (length m + 1) and wrap_x / wrap_y say
+    whether some cluster winds round the torus along x / y."""
+    acc = np.ascontiguousarray(accepted, dtype=np.uint32)
+    if not 0 <= m <= acc.size:
+        raise ValueError("m out of range")
+    counts = np.zeros(m + 1, dtype=np.int64)
+    w = ctypes.c_int32(0)
+    rc = _load().oracle_configuration(L, k, acc.ctypes.data, m, counts.ctypes.data, m + 1,
+                                      ctypes.byref(w))
+    if rc != 0:
+        raise MemoryError("oracle_configuration failed rc=%d" % rc)
+    return counts, bool(w.value & 1), bool(w.value & 2)
 
 
 def max_free_runs(occ: np.ndarray):

@@ -58,6 +58,37 @@ def wraps(L: int, occupied) -> bool:
     return False
 
 
+def wrap_dirs(L: int, occupied):
+    """(winds along x, winds along y) for the occupied cells: the same lifted
+    breadth-first search as :func:`wraps`, run to the end; every edge that
+    reaches an already-lifted cell at another lift is a cycle whose winding is
+    (lift difference) / L, and a direction counts if any such cycle moves
+    along it."""
+    occ = set(occupied)
+    lift = {}
+    wx = wy = False
+    for start in occ:
+        if start in lift:
+            continue
+        lift[start] = start
+        q = deque([start])
+        while q:
+            a = q.popleft()
+            ly, lx = lift[a]
+            for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+                b = ((a[0] + dy) % L, (a[1] + dx) % L)
+                if b not in occ:
+                    continue
+                want = (ly + dy, lx + dx)
+                if b in lift:
+                    wy |= lift[b][0] != want[0]
+                    wx |= lift[b][1] != want[1]
+                else:
+                    lift[b] = want
+                    q.append(b)
+    return wx, wy
+
+
 def clusters(L: int, occupied):
     """List of clusters (sets of cells), 4-neighbour connectivity on the torus."""
     occ = set(occupied)

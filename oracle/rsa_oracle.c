@@ -369,3 +369,85 @@ int oracle_contacts(uint32_t L, uint32_t k, const uint32_t *accepted, int64_t nj
     *nx = cx; *ny = cy; *nxy = cxy;
     return 0;
 }
+
+/* ---- the configuration of the first m accepted k-mers (Sec. II.C, II.D,
+ * Sec. III "Structure of the percolating and jamming states") -------------
+ *
+ * Clusters are the connected components of occupied cells, 4-neighbours on
+ * the torus.  Every lattice edge (a, a + e), e = +x or +y, whose two cells
+ * are occupied is a constraint lift(a) + e = lift(a + e) on the lifted
+ * (unwrapped) positions, lift(cell) = lift(anchor) + j e(k-mer) for the
+ * cell's position j inside its k-mer.  Union-find over k-mers keeps the
+ * exact int64 displacement of every k-mer's anchor from its root; an edge
+ * inside one cluster whose two lifts disagree closes a cycle that winds
+ * round the torus, by (mismatch_x / L, mismatch_y / L) turns.
+ *
+ *   counts[s] (s = 0 .. cap-1) = number of clusters made of exactly s
+ *       k-mers (s k sites); needs cap >= m + 1, else -1.  May be NULL.
+ *   *wrap (may be NULL) = bit 0: some cluster winds round the torus along
+ *       x, bit 1: along y (any cycle with a non-zero x / y winding).
+ * Returns 0, -1 on a short counts array, -2 on allocation failure. */
+int oracle_configuration(uint32_t L, uint32_t k, const uint32_t *accepted, int64_t m,
+                         int64_t *counts, int64_t cap, int32_t *wrap)
+{
+    size_t LL = (size_t)L * L;
+    if (counts && cap < m + 1) return -1;
+    int64_t *who = (int64_t *)malloc(LL * sizeof(int64_t));
+    int64_t *jpos = (int64_t *)malloc(LL * sizeof(int64_t));
+    orc_uf u;
+    u.parent = (int32_t *)malloc((size_t)(m + 1) * sizeof(int32_t));
+    u.dx = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    u.dy = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    u.size = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    if (!who || !jpos || !u.parent || !u.dx || !u.dy || !u.size) {
+        free(who); free(jpos); free(u.parent); free(u.dx); free(u.dy); free(u.size);
+        return -2;
+    }
+    for (size_t i = 0; i < LL; ++i) who[i] = -1;
+    for (int64_t a = 0; a < m; ++a) {
+        u.parent[a] = (int32_t)a; u.dx[a] = 0; u.dy[a] = 0; u.size[a] = 1;
+        for (uint32_t i = 0; i < k; ++i) {
+            uint32_t y, x;
+            orc_cell(L, accepted[a], i, &y, &x);
+            who[(size_t)y * L + x] = a;
+            jpos[(size_t)y * L + x] = i;
+        }
+    }
+    int32_t w = 0;
+    for (uint32_t y = 0; y < L; ++y)
+        for (uint32_t x = 0; x < L; ++x) {
+            int64_t a = who[(size_t)y * L + x];
+            if (a < 0) continue;
+            for (int d = 0; d < 2; ++d) {             /* e = +x, then +y */
+                uint32_t by = d ? (y + 1) % L : y, bx = d ? x : (x + 1) % L;
+                int64_t b = who[(size_t)by * L + bx];
+                if (b < 0) continue;
+                int va = accepted[a] >= LL, vb = accepted[b] >= LL;   /* 1 = vertical */
+                int64_t ja = jpos[(size_t)y * L + x], jb = jpos[(size_t)by * L + bx];
+                int64_t oax, oay, obx, oby;
+                int32_t ra = orc_find(&u, (int32_t)a, &oax, &oay);
+                int32_t rb = orc_find(&u, (int32_t)b, &obx, &oby);
+                /* lift(a) + e and lift(b), each relative to its own root */
+                int64_t px = oax + (va ? 0 : ja) + (d == 0), py = oay + (va ? ja : 0) + (d == 1);
+                int64_t qx = obx + (vb ? 0 : jb), qy = oby + (vb ? jb : 0);
+                if (ra == rb) {
+                    if (px != qx) w |= 1;
+                    if (py != qy) w |= 2;
+                } else if (u.size[ra] >= u.size[rb]) {   /* rb sits at p - q from ra */
+                    u.parent[rb] = ra; u.dx[rb] = px - qx; u.dy[rb] = py - qy;
+                    u.size[ra] += u.size[rb];
+                } else {
+                    u.parent[ra] = rb; u.dx[ra] = qx - px; u.dy[ra] = qy - py;
+                    u.size[rb] += u.size[ra];
+                }
+            }
+        }
+    if (counts) {
+        for (int64_t s = 0; s < cap; ++s) counts[s] = 0;
+        for (int64_t a = 0; a < m; ++a)
+            if (u.parent[a] == (int32_t)a) counts[u.size[a]] += 1;
+    }
+    if (wrap) *wrap = w;
+    free(who); free(jpos); free(u.parent); free(u.dx); free(u.dy); free(u.size);
+    return 0;
+}

@@ -12,6 +12,9 @@ not against the oracle itself.
 * Appendix A Proposition: every cluster of every jammed packing wraps
   (exhaustive on small tori), hence n_c <= n_j.
 * Statistics against Table I and the known k = 1 and k = 2 values.
+* The configuration of the first m k-mers (cluster-size histogram, winding
+  directions) against breadth-first search on the lifted lattice, its
+  transpose symmetry, and the Fisher exponent of Eq. CSD at k = 1.
 """
 import itertools
 import math
@@ -292,3 +295,97 @@ def test_contacts_match_brute_force_and_edge_count(L, k):
         inner = acc.size * (k if k == L else k - 1)
         if L > 2:
             assert sum(got) == edges - inner
+
+
+def test_wrap_dirs_checker_basic_shapes():
+    assert brute.wrap_dirs(5, [(2, x) for x in range(5)]) == (True, False)
+    assert brute.wrap_dirs(5, [(y, 3) for y in range(5)]) == (False, True)
+    assert brute.wrap_dirs(5, [(2, x) for x in range(4)]) == (False, False)
+    ring = [(1, 1), (1, 2), (1, 3), (2, 3), (3, 3), (3, 2), (3, 1), (2, 1)]
+    assert brute.wrap_dirs(6, ring) == (False, False)
+    # winding (1, 1): one turn along x and one along y
+    stair = [(i, i) for i in range(4)] + [(i, i + 1) for i in range(3)] + [(3, 0)]
+    assert brute.wrap_dirs(4, stair) == (True, True)
+    # a row plus a column: both directions, as two separate cycles
+    cross = [(0, x) for x in range(6)] + [(y, 2) for y in range(1, 6)]
+    assert brute.wrap_dirs(6, cross) == (True, True)
+    # L = 1: the +x and +y edges of the only cell are both self-loops
+    assert brute.wrap_dirs(1, [(0, 0)]) == (True, True)
+    assert brute.wrap_dirs(2, [(0, 0), (0, 1)]) == (True, False)
+
+
+def _transpose(L, acc):
+    """Candidates mirrored in the diagonal: H(y, x) <-> V(x, y)."""
+    LL = L * L
+    a = np.asarray(acc, dtype=np.int64)
+    o, r = np.divmod(a, LL)
+    y, x = np.divmod(r, L)
+    return (((1 - o) * L + x) * L + y).astype(np.uint32)
+
+
+@pytest.mark.parametrize("L,k", [(1, 1), (2, 1), (2, 2), (3, 1), (4, 2), (5, 2), (6, 3),
+                                 (7, 1), (8, 2), (8, 4), (9, 3), (10, 10), (12, 4)])
+def test_configuration_matches_bfs_on_the_lift(L, k):
+    for seed in range(1, 13 if L <= 8 else 6):
+        nj, nc, _, acc = oracle.sample_keys(L, k, oracle.keys(L, seed))
+        for m in range(nj + 1):
+            counts, wx, wy = oracle.configuration(L, k, acc, m)
+            cells = [c for idx in acc[:m] for c in brute.cells_of(L, k, int(idx))]
+            want = np.zeros(m + 1, dtype=np.int64)
+            for comp in brute.clusters(L, cells):
+                assert len(comp) % k == 0
+                want[len(comp) // k] += 1
+            assert np.array_equal(counts, want), (seed, m)
+            assert (wx, wy) == brute.wrap_dirs(L, cells), (seed, m)
+            # Sec. II.D: a cluster wraps from the n_c-th k-mer on
+            assert (wx or wy) == (m >= nc), (seed, m, nc)
+
+
+@pytest.mark.parametrize("L,k", [(16, 2), (32, 4), (48, 8), (64, 1)])
+def test_configuration_invariants(L, k):
+    for seed in range(1, 6):
+        nj, nc, _, acc = oracle.sample_keys(L, k, oracle.keys(L, seed))
+        accT = _transpose(L, acc)
+        for m in sorted({1, nc - 1, nc, nj, (nc + nj) // 2}):
+            counts, wx, wy = oracle.configuration(L, k, acc, m)
+            assert int(np.sum(np.arange(m + 1) * counts)) == m   # every k-mer once
+            assert counts[0] == 0
+            cT, wxT, wyT = oracle.configuration(L, k, accT, m)
+            assert np.array_equal(cT, counts) and (wxT, wyT) == (wy, wx)
+        # Appendix A Proposition: at jamming every cluster wraps, so the
+        # lattice winds in some direction
+        _, wx, wy = oracle.configuration(L, k, acc, nj)
+        assert wx or wy
+
+
+@pytest.mark.parametrize("L", [1, 3, 8])
+def test_configuration_of_a_ring(L):
+    # k = L: one k-mer closes on itself and winds along its own axis
+    for o, want in ((0, (True, False)), (1, (False, True))):
+        counts, wx, wy = oracle.configuration(L, L, np.array([o * L * L], dtype=np.uint32), 1)
+        assert list(counts) == [0, 1]
+        if L > 1:
+            assert (wx, wy) == want
+        else:
+            assert (wx, wy) == (True, True)
+
+
+def test_cluster_sizes_follow_the_fisher_exponent():
+    # Eq. CSD: at the percolation threshold n_s ~ s^-tau, tau = 187/91, for
+    # large s.  Site percolation (k = 1) at the first wrap, L = 256, 40
+    # samples, log-binned s in [4, 1024]; corrections to scaling at these
+    # sizes make the apparent slope somewhat shallower than -tau.
+    L, k, N = 256, 1, 40
+    tot = np.zeros(L * L + 1)
+    for seed in range(1, N + 1):
+        _, nc, _, acc = oracle.sample_keys(L, k, oracle.keys(L, seed))
+        counts, _, _ = oracle.configuration(L, k, acc, nc)
+        tot[:counts.size] += counts
+    s = np.arange(tot.size) * k
+    xs, ys = [], []
+    for a in 2.0 ** np.arange(2, 10):
+        sel = (s >= a) & (s < 2 * a)
+        xs.append(a * math.sqrt(2))
+        ys.append(tot[sel].sum() / N / (L * L) / a)
+    slope = np.polyfit(np.log(xs), np.log(ys), 1)[0]
+    assert abs(slope + 187 / 91) < 0.25, slope
