@@ -296,7 +296,7 @@ def main():
     assert np.array_equal(nj_h, nj) and np.array_equal(nc_h, nc)
 
     # ---- the plain path: one sample per run call, for comparison ----
-    plain_n = 16
+    plain_n = min(16, n)
     barrier()
     t0 = time.perf_counter()
     for i in range(plain_n):

@@ -109,6 +109,32 @@ int rsa_sample_stats(rsa_t *h, uint32_t *rounds, uint32_t *probes, uint32_t *edg
  * Host arrays of length n (any may be NULL). */
 int rsa_contacts(rsa_t *h, uint32_t *n_x, uint32_t *n_y, uint32_t *n_xy, uint32_t n);
 
+/* The configuration of the first m accepted k-mers (in RSA order) of sample
+ * `sample` of the last run, 0 <= m <= n_j: m = n_c is the percolating state
+ * and m = n_j the jamming state of Sec. III ("Structure of the percolating
+ * and jamming states").  Clusters are connected components of occupied
+ * sites, 4-neighbours on the torus (Sec. II.C).
+ *
+ * rsa_cluster_sizes: counts[s] = number of clusters made of exactly s k-mers
+ *   (s k sites), s = 0 .. m; counts[0] = 0 and the sum of s counts[s] is m.
+ *   n_s of Eq. CSD is counts[s] / L^2 for cluster size s k.  counts is a
+ *   caller-owned host array of cap >= m + 1 entries (RSA_EINVAL otherwise);
+ *   entries past m are zeroed.
+ * rsa_wrap_dirs: *wrap_x (*wrap_y) = 1 iff some cluster winds round the
+ *   torus along x (y) (Sec. II.D, "in one or both directions"); either
+ *   pointer may be NULL.  The directions are those of the closed cycles'
+ *   windings (a, b), decided from a L and b L modulo 2^16: exact whenever
+ *   |a|, |b| < 2^16 / 2^v (2^v the largest power of two dividing L), which
+ *   covers any cycle shorter than 2^16 L / 2^v lattice steps.
+ *
+ * Both run on the stream of the last run and return when the result is on
+ * the host; they reuse that sample's union-find scratch, so call them after
+ * rsa_results.  RSA_EINVAL for a bad sample, m or array; the sample's own
+ * error code if it has no valid result; RSA_ETIMEOUT if a union-find walk hit
+ * its cap. */
+int rsa_cluster_sizes(rsa_t *h, uint32_t sample, uint32_t m, uint32_t *counts, uint32_t cap);
+int rsa_wrap_dirs(rsa_t *h, uint32_t sample, uint32_t m, uint32_t *wrap_x, uint32_t *wrap_y);
+
 /* TEST ONLY: the accepted candidates (idx) of sample `sample` of the last run,
  * sorted ascending; *count receives n_j; at most cap values are written. */
 int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_t *count);

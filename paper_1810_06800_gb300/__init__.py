@@ -6,4 +6,4 @@ Importing the package is cheap; the CUDA library is loaded by
 :mod:`paper_1810_06800_gb300.rsa` on first use and fails loudly if it is
 missing."""
 
-__all__ = ["rsa", "workloads"]
+__all__ = ["rsa", "workloads", "study", "serve"]

@@ -20,6 +20,7 @@
 #include "rsa_kernels.cuh"
 #include "rsa_tile.cuh"
 #include "rsa_line.cuh"
+#include "rsa_config.cuh"
 
 using namespace rsak;
 
@@ -202,12 +203,13 @@ int set_smem(F* fn, size_t bytes) {
 enum Kind {
   KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
   KD_LINE_CMIN_H, KD_LINE_CMIN_V, KD_LINE_COMBINE, KD_LINE_ACCEPT_H, KD_LINE_ACCEPT_V,
+  KD_LINE_CODES,
   KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE, KD_COUNT
 };
 const char* const kKindNames[KD_COUNT] = {
     "k_init",         "k_row_cmin",    "k_col_cmin",   "k_row_accept", "k_col_accept",
     "k_tile_cmin",    "k_tile_accept", "k_line_cmin_h", "k_line_cmin_v", "k_line_combine",
-    "k_line_accept_h", "k_line_accept_v", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
+    "k_line_accept_h", "k_line_accept_v", "k_line_codes", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
     "k_probe_copy",   "k_probe",       "k_search_decide"};
 
 // Optional per-kernel timing with CUDA events recorded around each launch
@@ -542,7 +544,7 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
         } else {
           u16* c16 = reinterpret_cast<u16*>(b + l.code16);
           u16* c16T = reinterpret_cast<u16*>(b + l.code16T);
-          launch(h, KD_LINE_COMBINE, k_line_codes, tg, dim3(256), 0, st, g, (const u64*)g.cmin,
+          launch(h, KD_LINE_CODES, k_line_codes, tg, dim3(256), 0, st, g, (const u64*)g.cmin,
                  (const u64*)cB, c16, c16T);
           launch(h, KD_LINE_ACCEPT_H, k_line_accept_codes<0>, lg, dim3(LINE_THREADS),
                  G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T);
@@ -670,6 +672,53 @@ int static_workspace(void** out) {
     g_static_ptr[dev] = p;
   }
   *out = g_static_ptr[dev];
+  return 0;
+}
+
+// The configuration of the first m accepted k-mers of sample `sample` of
+// the last run: winding bits into *wdirs, and, if counts is given, the
+// cluster-size histogram counts[0 .. m] (cap >= m + 1).
+int configuration(rsa_t* h, uint32_t sample, uint32_t m, uint32_t* counts, uint32_t cap,
+                  uint32_t* wdirs) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  if (sample >= h->last_n) return fail(RSA_EINVAL, "sample out of range");
+  if (counts && cap < (u64)m + 1) return fail(RSA_EINVAL, "counts needs m + 1 entries");
+  std::vector<SampleState> st;
+  int rc = fetch_states(h, st);
+  if (rc) return rc;
+  if ((rc = status_code(st[sample].status))) {
+    g_err = "sample " + std::to_string(sample) + " has no valid result";
+    return rc;
+  }
+  const u32 nj = st[sample].n_nodes;
+  if (m > nj) return fail(RSA_EINVAL, "m exceeds n_j of the sample");
+  if (counts) std::memset(counts, 0, (size_t)cap * sizeof(uint32_t));
+  *wdirs = 0;
+  if (m == 0) return 0;
+  cudaStream_t stream = h->stream;
+  Group g = group_of(h, h->last_n);
+  const u32 bx = (u32)std::min<u64>(((u64)g.cap_edges + 255) / 256, 2048);
+  const u32 nb = (u32)std::min<u64>(((u64)nj + 256) / 256, 1024);
+  k_select_key<<<1, 1024, 0, stream>>>(g, sample, m);
+  k_cfg_init<<<nb, 256, 0, stream>>>(g, sample);
+  k_cfg_union<<<bx, 256, 0, stream>>>(g, sample);
+  if (counts) {
+    k_cfg_count<<<nb, 256, 0, stream>>>(g, sample);
+    k_cfg_hist<<<nb, 256, 0, stream>>>(g, sample);
+  }
+  CUDA_TRY(cudaGetLastError());
+  const char* b = static_cast<const char*>(h->ws);
+  const size_t so = h->lay.st + (size_t)sample * sizeof(SampleState);
+  CUDA_TRY(cudaMemcpyAsync(h->h_counter + 12, b + so + offsetof(SampleState, wdirs), 4,
+                           cudaMemcpyDeviceToHost, stream));
+  if (counts)
+    CUDA_TRY(cudaMemcpyAsync(counts,
+                             b + h->lay.edges + (size_t)sample * g.cap_edges * sizeof(Edge),
+                             ((size_t)m + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(cudaStreamSynchronize(stream));
+  const u32 w = h->h_counter[12];
+  if (w & CFG_CAPPED) return fail(RSA_ETIMEOUT, "union-find walk cap reached");
+  *wdirs = w & 3u;
   return 0;
 }
 
@@ -829,6 +878,21 @@ int rsa_accepted(rsa_t* h, uint32_t sample, uint32_t* idx, uint32_t cap, uint32_
   std::sort(v.begin(), v.end());
   *count = nj;
   if (idx) std::memcpy(idx, v.data(), (size_t)std::min(cap, nj) * 4);
+  return 0;
+}
+
+int rsa_cluster_sizes(rsa_t* h, uint32_t sample, uint32_t m, uint32_t* counts, uint32_t cap) {
+  if (!counts) return fail(RSA_EINVAL, "null counts");
+  uint32_t w;
+  return configuration(h, sample, m, counts, cap, &w);
+}
+
+int rsa_wrap_dirs(rsa_t* h, uint32_t sample, uint32_t m, uint32_t* wrap_x, uint32_t* wrap_y) {
+  uint32_t w = 0;
+  int rc = configuration(h, sample, m, nullptr, 0, &w);
+  if (rc) return rc;
+  if (wrap_x) *wrap_x = w & 1u;
+  if (wrap_y) *wrap_y = (w >> 1) & 1u;
   return 0;
 }
 

@@ -78,8 +78,11 @@ struct SampleState {   // one per sample, 128 bytes
   u32 cur, sdone, nc, hi_ok;
   u32 contacts_x, contacts_y, contacts_xy;  // lattice edges between different
                                             // k-mers: both H, both V, mixed
-  u32 pad[7];
+  u32 wdirs;                                // configuration pass: winding bits
+  u64 sel;                                  // configuration pass: m-th key
+  u32 pad[4];
 };
+static_assert(sizeof(SampleState) == 128, "SampleState is 128 bytes");
 
 struct Group {         // one batch of samples sharing (L, k)
   u32 L, k, n;

@@ -424,9 +424,11 @@ __device__ __forceinline__ u32 uf_find(u64* W, u32 x, u32* ox, u32* oy, bool* ca
 }
 
 // Add edge "anchor(m2) = anchor(m1) + d"; returns true if it closes a cycle
-// of non-zero winding.  Roots are linked larger-id under smaller-id, so the
-// forest stays acyclic under concurrent unions.
-__device__ bool uf_union(u64* W, u32 m1, u32 m2, u32 dxy, bool* capped) {
+// of non-zero winding, and then, if mis is given, stores the cycle's lifted
+// mismatch (x in bits 0-15, y in 16-31, modulo 2^16).  Roots are linked
+// larger-id under smaller-id, so the forest stays acyclic under concurrent
+// unions.
+__device__ bool uf_union(u64* W, u32 m1, u32 m2, u32 dxy, bool* capped, u32* mis = nullptr) {
   const u32 dx = dxy & 0xFFFFu, dy = dxy >> 16;
   for (u32 it = 0; it < UF_CAP; ++it) {
     u32 o1x, o1y, o2x, o2y;
@@ -435,7 +437,10 @@ __device__ bool uf_union(u64* W, u32 m1, u32 m2, u32 dxy, bool* capped) {
     if (*capped) return false;
     // lifted position of r2 minus r1
     const u32 Dx = o1x + dx - o2x, Dy = o1y + dy - o2y;
-    if (r1 == r2) return ((Dx | Dy) & 0xFFFFu) != 0;
+    if (r1 == r2) {
+      if (mis) *mis = (Dx & 0xFFFFu) | ((Dy & 0xFFFFu) << 16);
+      return ((Dx | Dy) & 0xFFFFu) != 0;
+    }
     if (r1 < r2) {
       if (atomicCAS(W + r2, uf_pack(r2, 0, 0), uf_pack(r1, Dx, Dy)) == uf_pack(r2, 0, 0))
         return false;

@@ -21,7 +21,8 @@ _NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_EC
           RSA_ETIMEOUT: "RSA_ETIMEOUT", RSA_ENOWRAP: "RSA_ENOWRAP", RSA_ESTATE: "RSA_ESTATE"}
 SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_run_static",
            "rsa_results",
-           "rsa_sample_stats", "rsa_contacts", "rsa_accepted", "rsa_workspace_bytes", "rsa_bind_workspace",
+           "rsa_sample_stats", "rsa_contacts", "rsa_cluster_sizes", "rsa_wrap_dirs", "rsa_accepted",
+           "rsa_workspace_bytes", "rsa_bind_workspace",
            "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
@@ -56,6 +57,8 @@ def load():
     lib.rsa_results.argtypes = [vp, vp, vp, u32]
     lib.rsa_sample_stats.argtypes = [vp, vp, vp, vp, vp, u32]
     lib.rsa_contacts.argtypes = [vp, vp, vp, vp, u32]
+    lib.rsa_cluster_sizes.argtypes = [vp, u32, u32, vp, u32]
+    lib.rsa_wrap_dirs.argtypes = [vp, u32, u32, ctypes.POINTER(u32), ctypes.POINTER(u32)]
     lib.rsa_accepted.argtypes = [vp, u32, vp, u32, ctypes.POINTER(u32)]
     lib.rsa_workspace_bytes.argtypes = [u32, u32, u32, ctypes.POINTER(u64)]
     lib.rsa_bind_workspace.argtypes = [vp, vp, u64]
@@ -152,6 +155,21 @@ def rsa_contacts(h, n: int):
     return a, b, c
 
 
+def rsa_cluster_sizes(h, sample: int, m: int):
+    """counts[s] = clusters of exactly s k-mers among the first m accepted
+    k-mers of `sample` (uint32, length m + 1)."""
+    out = np.zeros(m + 1, dtype=np.uint32)
+    _check(load().rsa_cluster_sizes(h, sample, m, out.ctypes.data, m + 1))
+    return out
+
+
+def rsa_wrap_dirs(h, sample: int, m: int):
+    """(winds along x, winds along y) for the first m accepted k-mers."""
+    wx, wy = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(load().rsa_wrap_dirs(h, sample, m, ctypes.byref(wx), ctypes.byref(wy)))
+    return bool(wx.value), bool(wy.value)
+
+
 def rsa_accepted(h, sample: int):
     cnt = ctypes.c_uint32()
     _check(load().rsa_accepted(h, sample, None, 0, ctypes.byref(cnt)))
@@ -237,6 +255,20 @@ class Lattice:
 
     def accepted(self, sample=0):
         return rsa_accepted(self.h, sample)
+
+    def _m(self, sample, m):
+        if m is None:   # the percolating state: m = n_c
+            _, nc = rsa_results(self.h, sample + 1)
+            m = int(nc[sample])
+        return m
+
+    def cluster_sizes(self, sample=0, m=None):
+        """Cluster-size histogram of the first m k-mers (default m = n_c)."""
+        return rsa_cluster_sizes(self.h, sample, self._m(sample, m))
+
+    def wrap_dirs(self, sample=0, m=None):
+        """Winding directions of the first m k-mers (default m = n_c)."""
+        return rsa_wrap_dirs(self.h, sample, self._m(sample, m))
 
     def close(self):
         rsa_destroy(self.h)

@@ -389,3 +389,19 @@ def test_cluster_sizes_follow_the_fisher_exponent():
         ys.append(tot[sel].sum() / N / (L * L) / a)
     slope = np.polyfit(np.log(xs), np.log(ys), 1)[0]
     assert abs(slope + 187 / 91) < 0.25, slope
+
+
+def test_horizontal_wrapping_probability_at_pc():
+    # Appendix A (proof of the Consequence): at p = p_c the probability that a
+    # cluster wraps horizontally tends to R* = 0.521058290 (k = 1, site
+    # percolation, p_c = 0.592746).  L = 128, 400 samples, both axes averaged
+    # (standard error about 0.02).
+    L, k, N = 128, 1, 400
+    m = round(0.592746 * L * L)
+    wx = wy = 0
+    for seed in range(1, N + 1):
+        _, _, _, acc = oracle.sample_keys(L, k, oracle.keys(L, seed))
+        _, x, y = oracle.configuration(L, k, acc, m)
+        wx += x
+        wy += y
+    assert abs((wx + wy) / (2 * N) - 0.521058290) < 0.06, (wx / N, wy / N)
