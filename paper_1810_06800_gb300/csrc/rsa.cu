@@ -365,6 +365,10 @@ int read_counter(rsa_t* h, u32* dev_counter, u32* out) {
 
 template <int K>
 int tile_occ_k(rsa_t* h) {
+  // the cell-minimum pass is sized for six resident blocks of ~38 KB static
+  // shared memory: ask for the largest shared-memory carveout
+  CUDA_TRY(cudaFuncSetAttribute(k_tile_cmin<K>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared));
   CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[0], k_tile_cmin<K>, TILE_THREADS, 0));
   CUDA_TRY(
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&h->tile_blocks[1], k_tile_accept<K>, TILE_THREADS, 0));

@@ -37,115 +37,26 @@ __device__ __forceinline__ u64 kmask() {
   return K >= 64 ? ~0ull : ((1ull << K) - 1ull);
 }
 
-// Backward window along one line held in shared memory, one thread:
-//   ln[32 + x] := min(ln[32 + x - K + 1 .. 32 + x])   for x in [0, 32),
-// the line holding positions -32 .. 31 at ln[0 .. 63] (negative positions =
-// the tile before).  van Herk / Gil-Werman with K-aligned blocks: suffix
-// minima Q of the previous block in registers, running prefix minimum P of
-// the current one, window = min(Q[i+1], P).  In place: position p is read
-// before it is overwritten.
-template <int K>
-__device__ __forceinline__ void line_bwd(u64* ln) {
-  constexpr int NB = 32 / K;
-  u64 q[K];
-  q[0] = KEY_NONE;
-#pragma unroll
-  for (int j = 1; j < K; ++j) q[j] = ln[32 - K + j];
-#pragma unroll
-  for (int j = K - 2; j >= 0; --j) q[j] = tmin(q[j], q[j + 1]);
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    u64 w[K];
-    u64 P = KEY_NONE;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      const u64 v = ln[32 + b * K + i];
-      if (b + 1 < NB) w[i] = v;
-      P = tmin(P, v);
-      ln[32 + b * K + i] = (i + 1 < K) ? tmin(q[(i + 1) % K], P) : P;
-    }
-    if (b + 1 < NB) {
-#pragma unroll
-      for (int j = K - 2; j >= 0; --j) w[j] = tmin(w[j], w[j + 1]);
-#pragma unroll
-      for (int j = 0; j < K; ++j) q[j] = w[j];
-    }
-  }
-}
+// Line buffers.  A tile line (a row for horizontal candidates, a column for
+// vertical ones) holds the live priorities of the candidates anchored at
+// positions p = -31 .. 31 along it (negative = the tile before) at slot
+// SLOT(p) = 31 + p; position -32 is in no window of k <= 32 cells that
+// reaches the tile.  LN = 63 u64 slots: odd, so 32 threads walking 32 lines
+// at the same slot hit distinct banks.  The byte buffers of argmin offsets
+// use the same slots with a 68-byte pitch (17 words, also conflict-free).
+constexpr int LN = 63;
+constexpr int LA = 68;
+__host__ __device__ constexpr int SLOT(int p) { return 31 + p; }
 
-// Forward window along one line in shared memory, one thread:
-//   ln[x] := min(ln[x .. x + K - 1])   for x in [0, 32),  ln[0 .. 32+K-2] valid.
-// Suffix minima Q of block b, running prefix minimum of block b+1.  In place.
-template <int K>
-__device__ __forceinline__ void line_fwd(u64* ln) {
-  constexpr int NB = 32 / K;
-  u64 q[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) q[j] = ln[j];
-#pragma unroll
-  for (int j = K - 2; j >= 0; --j) q[j] = tmin(q[j], q[j + 1]);
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    u64 w[K];
-    u64 P = KEY_NONE;
-    ln[b * K] = q[0];
-#pragma unroll
-    for (int i = 0; i + 1 < K; ++i) {
-      const u64 v = ln[(b + 1) * K + i];
-      if (b + 1 < NB) w[i] = v;
-      P = tmin(P, v);
-      ln[b * K + i + 1] = tmin(q[(i + 1) % K], P);
-    }
-    if (b + 1 < NB) {
-      w[K - 1] = ln[(b + 1) * K + K - 1];
-#pragma unroll
-      for (int j = K - 2; j >= 0; --j) w[j] = tmin(w[j], w[j + 1]);
-#pragma unroll
-      for (int j = 0; j < K; ++j) q[j] = w[j];
-    }
-  }
-}
-
-// K = 32 variants of line_bwd / line_fwd that keep the suffix minima in the
-// shared-memory line itself instead of 32 64-bit registers (one block per
-// line, so no second block's values need to survive).
-__device__ __forceinline__ void line_bwd32_smem(u64* ln) {
-  u64 q = KEY_NONE;
-#pragma unroll 8
-  for (int j = 31; j >= 1; --j) {
-    q = tmin(q, ln[j]);
-    ln[j] = q;
-  }
-  u64 P = KEY_NONE;
-#pragma unroll 8
-  for (int i = 0; i < 31; ++i) {
-    P = tmin(P, ln[32 + i]);
-    ln[32 + i] = tmin(ln[i + 1], P);
-  }
-  ln[63] = tmin(P, ln[63]);
-}
-
-__device__ __forceinline__ void line_fwd32_smem(u64* ln) {
-  u64 q = ln[31];
-#pragma unroll 8
-  for (int j = 30; j >= 0; --j) {
-    q = tmin(q, ln[j]);
-    ln[j] = q;
-  }
-  u64 P = KEY_NONE;
-#pragma unroll 8
-  for (int i = 0; i < 31; ++i) {
-    P = tmin(P, ln[32 + i]);
-    ln[i + 1] = tmin(ln[i + 1], P);
-  }
-}
-
-// Argmin-tracking variants for the cell-minimum pass.  Besides the window
-// minimum they record, per output cell, the offset d = cell - anchor of the
-// candidate that achieved it (0 .. K-1), or ARG_NONE when the window has no
-// live candidate.  la is the line's byte buffer (same slots as ln).
 constexpr u8 ARG_NONE = 0xFF;
 
+// Backward window minima with argmin, one thread per line, K < 32:
+//   ln[SLOT(x)] := min(live priorities anchored at x-K+1 .. x),  x in [0, 32),
+//   la[SLOT(x)] := x - (anchor of that minimum), or ARG_NONE if none.
+// van Herk / Gil-Werman with K-aligned blocks (K divides 32, so blocks align
+// with the tile): suffix minima Q of the previous block in registers, running
+// prefix minimum P of the current one, window = min(Q[i+1], P).  In place:
+// a slot is read before it is overwritten.
 template <int K>
 __device__ __forceinline__ void line_bwd_arg(u64* ln, u8* la) {
   constexpr int NB = 32 / K;
@@ -154,7 +65,7 @@ __device__ __forceinline__ void line_bwd_arg(u64* ln, u8* la) {
   q[0] = KEY_NONE;
   qa[0] = 0;
 #pragma unroll
-  for (int j = 1; j < K; ++j) { q[j] = ln[32 - K + j]; qa[j] = j; }
+  for (int j = 1; j < K; ++j) { q[j] = ln[SLOT(j - K)]; qa[j] = j; }
 #pragma unroll
   for (int j = K - 2; j >= 0; --j)
     if (q[j + 1] < q[j]) { q[j] = q[j + 1]; qa[j] = qa[j + 1]; }
@@ -166,7 +77,7 @@ __device__ __forceinline__ void line_bwd_arg(u64* ln, u8* la) {
     int pa = 0;
 #pragma unroll
     for (int i = 0; i < K; ++i) {
-      const u64 v = ln[32 + b * K + i];
+      const u64 v = ln[SLOT(b * K + i)];
       if (b + 1 < NB) { w[i] = v; wa[i] = i; }
       if (v < P) { P = v; pa = i; }
       u64 out = P;
@@ -175,8 +86,8 @@ __device__ __forceinline__ void line_bwd_arg(u64* ln, u8* la) {
         out = q[(i + 1) % K];
         d = i + K - qa[(i + 1) % K];
       }
-      ln[32 + b * K + i] = out;
-      la[32 + b * K + i] = out == KEY_NONE ? ARG_NONE : (u8)d;
+      ln[SLOT(b * K + i)] = out;
+      la[SLOT(b * K + i)] = out == KEY_NONE ? ARG_NONE : (u8)d;
     }
     if (b + 1 < NB) {
 #pragma unroll
@@ -188,36 +99,20 @@ __device__ __forceinline__ void line_bwd_arg(u64* ln, u8* la) {
   }
 }
 
-// K = 32: the suffix minima of the previous block stay in the shared line.
-__device__ __forceinline__ void line_bwd32_arg_smem(u64* ln, u8* la) {
-  u64 q = KEY_NONE;
-  int qa = 0;
-#pragma unroll 8
-  for (int j = 31; j >= 1; --j) {
-    const u64 v = ln[j];
-    if (v < q) { q = v; qa = j; }
-    ln[j] = q;
-    la[j] = (u8)qa;
-  }
-  u64 P = KEY_NONE;
-  int pa = 0;
-#pragma unroll 8
-  for (int i = 0; i < 32; ++i) {
-    const u64 v = ln[32 + i];
-    if (v < P) { P = v; pa = i; }
-    u64 out = P;
-    int d = i - pa;
-    if (i < 31) {
-      const u64 qv = ln[i + 1];
-      if (qv < P) { out = qv; d = i + 32 - la[i + 1]; }
+// Position (0-based rank n < popc(m)) of the n-th set bit of m.
+__device__ __forceinline__ u32 nth_set_bit(u32 m, u32 n) {
+  u32 pos = 0;
+#pragma unroll
+  for (u32 w = 16; w; w >>= 1) {
+    const u32 lo = __popc(m & ((1u << w) - 1u));
+    if (n >= lo) {
+      n -= lo;
+      m >>= w;
+      pos += w;
     }
-    ln[32 + i] = out;
-    la[32 + i] = out == KEY_NONE ? ARG_NONE : (u8)d;
   }
+  return pos;
 }
-
-constexpr int LN = 65;  // padded line length (u64) of the tile line buffers
-constexpr int LA = 68;  // line length of the byte buffers (17 words: conflict-free per line)
 
 // Asynchronous global -> shared copies (cp.async): a tile's staging loads are
 // all in flight together instead of one latency per loop iteration.
@@ -293,17 +188,24 @@ constexpr u32 TILE_THREADS = 128;
 // warps 0-1 take the tile's rows (horizontal candidates), warps 2-3 its
 // columns (vertical candidates), 16 lines each.
 //  (a) lane-parallel: live priorities of the candidates anchored on each line
-//      (and the K-1 positions before it) into line buffers lh[row][.],
-//      lv[col][.] (slot 32 + p = position p, p in -32 .. 31);
-//  (b) one thread per line: width-K backward window minima, in place;
-//  (c) cmin(y, x) = min(lh[y][32+x], lv[x][32+y]) written out coalesced.
+//      and the K-1 positions before it into the line buffers lh[row],
+//      lv[col]; a line with no live candidate is only marked, not written;
+//  (b) a tile with no live line is covered by no live candidate: flagged
+//      dead, nothing written;
+//  (c) one thread per live line: width-K backward window minima with argmin;
+//      for K = 32 one thread builds the suffix minima of the previous block
+//      and another the prefix minima of the tile's block, the write-out
+//      takes min(Q[x+1], P[x]);
+//  (d) argmin code of each cell (horizontal offset d, 32 + d vertical,
+//      ARG_NONE if uncovered) written out coalesced, 8 cells per store.
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc, u32* occw,
-                                                            u8* dead) {
+__global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
+    k_tile_cmin(Group g, TileCfg tc, u32* occw, u8* dead) {
   __shared__ u32 ow[96][3];     // occupancy words: rows Y-32 .. Y+63, word columns wx-1 .. wx+1
   __shared__ u64 lh[32][LN];
   __shared__ u64 lv[32][LN];
-  __shared__ u32 colmask[32][2];  // occupancy of each tile column: rows Y-32.., rows Y..
+  // occupancy of each tile column (rows Y-32.., rows Y..): short windows only
+  __shared__ u32 colmask[K < 16 ? 32 : 1][2];
   __shared__ u32 live_sh[2];      // per direction: bit r = line r has a live candidate
   __shared__ u8 ah[32][LA];       // argmin offsets of the row lines
   __shared__ u8 av[32][LA];       // argmin offsets of the column lines
@@ -329,13 +231,12 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
     // splitmix64 input of candidate idx is zb + gamma * idx
     const u64 zb = g.base[s] + SM_GAMMA;
     const bool caller = g.keys != nullptr;
-    u64 (*ln)[LN] = dirw == 0 ? lh : lv;
     u32 live = 0;    // lines of this warp with a live candidate (warp-uniform)
     u32 keyed = 0;   // live candidates this lane gave a key
     const u32 l0 = half * 16;
-    if (K >= 16) {
+    if constexpr (K >= 16) {
       // long windows: the K-1 positions before the tile are hashed in the
-      // same pass as the tile's own, lane = position
+      // same pass as the tile's own, lane = position (lane - 32 before it)
       const bool need_prev = lane >= 33u - K;
       if (dirw == 0) {
         const u64 zstep = SM_GAMMA * (u64)L;
@@ -347,7 +248,6 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
           const u64 B = ((u64)ow[32 + r][2] << 32) | ow[32 + r][1];  // positions 0 .. 63
           const bool ap = need_prev && ((A >> lane) & kmask<K>()) == 0;
           const bool ac = ((B >> lane) & kmask<K>()) == 0;
-          u64 vp = KEY_NONE, vc = KEY_NONE;
           if (__any_sync(FULL, ap || ac)) {
             u64 hp, hc;
             if (caller) {
@@ -357,13 +257,11 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
               hp = mix64(zp);
               hc = mix64(zc);
             }
-            vp = ap ? hp : KEY_NONE;
-            vc = ac ? hc : KEY_NONE;
+            if (need_prev) lh[r][SLOT((int)lane - 32)] = ap ? hp : KEY_NONE;
+            lh[r][SLOT(lane)] = ac ? hc : KEY_NONE;
             live |= 1u << r;
             keyed += (u32)ap + (u32)ac;
           }
-          lh[r][lane] = vp;
-          lh[r][32 + lane] = vc;
         }
       } else {
         const u32 bp = ow[lane][1], bc = ow[32 + lane][1], bn = ow[64 + lane][1];
@@ -378,7 +276,6 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
           const u64 A = ((u64)Mc << 32) | Mp, B = ((u64)Mn << 32) | Mc;
           const bool ap = need_prev && ((A >> lane) & kmask<K>()) == 0;
           const bool ac = ((B >> lane) & kmask<K>()) == 0;
-          u64 vp = KEY_NONE, vc = KEY_NONE;
           if (__any_sync(FULL, ap || ac)) {
             u64 hp, hc;
             if (caller) {
@@ -388,18 +285,15 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
               hp = mix64(zp);
               hc = mix64(zc);
             }
-            vp = ap ? hp : KEY_NONE;
-            vc = ac ? hc : KEY_NONE;
+            if (need_prev) lv[c][SLOT((int)lane - 32)] = ap ? hp : KEY_NONE;
+            lv[c][SLOT(lane)] = ac ? hc : KEY_NONE;
             live |= 1u << c;
             keyed += (u32)ap + (u32)ac;
           }
-          lv[c][lane] = vp;
-          lv[c][32 + lane] = vc;
         }
       }
-      if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
-      __syncthreads();
     } else {
+      u64 (*ln)[LN] = dirw == 0 ? lh : lv;
       if (dirw == 0) {
         // tile part of each row, lane = position along the row
         u64 z = zb + SM_GAMMA * ((u64)(Y + l0) * L + X + lane);
@@ -416,7 +310,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
             live |= 1u << r;
             keyed += (u32)ac;
           }
-          lh[r][32 + lane] = vc;
+          lh[r][SLOT(lane)] = vc;
         }
       } else {
         // tile part of each column, lane = position along the column
@@ -438,7 +332,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
             live |= 1u << c;
             keyed += (u32)ac;
           }
-          lv[c][32 + lane] = vc;
+          lv[c][SLOT(lane)] = vc;
         }
       }
       __syncthreads();  // colmask complete
@@ -462,96 +356,113 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_cmin(Group g, TileCfg tc,
           v = ap ? h : KEY_NONE;
           keyed += (u32)ap;
         }
-        ln[line][32 + pos] = v;
+        ln[line][SLOT(pos)] = v;
         live |= __reduce_or_sync(FULL, ap ? 1u << line : 0u);
       }
-      if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
-      __syncthreads();
     }
-    if (K == 32) {
-      // K = 32: every output window = suffix of the previous block + prefix
-      // of the tile's block; threads 0-63 build the suffix minima Q (slots
-      // 1..31), threads 64-127 the prefix minima P (slots 32..63) of the
-      // same 64 lines, in place with their argmin slots; the write-out below
-      // takes min(Q[x+1], P[x])
-      const u32 ln_id = threadIdx.x & 63;
-      u64* mine_ln = (ln_id < 32 ? lh : lv)[ln_id & 31];
-      u8* mine_la = (ln_id < 32 ? ah : av)[ln_id & 31];
-      if (threadIdx.x < 64) {
-        u64 q = KEY_NONE;
-        int qa = 0;
+    if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
+    __syncthreads();
+    const u32 lhb = live_sh[0], lvb = live_sh[1];
+    keyed = __reduce_add_sync(FULL, keyed);
+    if (lane == 0 && keyed) atomicAdd(g.work + 1, (u64)keyed);
+    if ((lhb | lvb) == 0) {
+      // no live candidate on or before any line: every cell is uncovered
+      if (threadIdx.x == 0) *dflag = 1;
+      __syncthreads();
+      continue;
+    }
+    if constexpr (K == 32) {
+      // live lines of both directions, numbered densely (rows first);
+      // thread t < 64 builds line t's suffix minima Q of the previous block
+      // (positions -31 .. -1, Q at SLOT(j - 32) = min over j .. 31, with its
+      // argmin j), thread 64 + t its prefix minima P of the tile's block
+      const u32 nh = __popc(lhb), nl = nh + __popc(lvb);
+      const u32 tt = threadIdx.x & 63;
+      if (tt < nl) {
+        const bool vert = tt >= nh;
+        const u32 line = vert ? nth_set_bit(lvb, tt - nh) : nth_set_bit(lhb, tt);
+        u64* ln = vert ? lv[line] : lh[line];
+        u8* la = vert ? av[line] : ah[line];
+        if (threadIdx.x < 64) {
+          u64 q = KEY_NONE;
+          int qa = 0;
 #pragma unroll 8
-        for (int j = 31; j >= 1; --j) {
-          const u64 v = mine_ln[j];
-          if (v < q) { q = v; qa = j; }
-          mine_ln[j] = q;
-          mine_la[j] = (u8)qa;
-        }
-      } else {
-        u64 P = KEY_NONE;
-        int pa = 0;
+          for (int j = 31; j >= 1; --j) {
+            const u64 v = ln[SLOT(j - 32)];
+            if (v < q) { q = v; qa = j; }
+            ln[SLOT(j - 32)] = q;
+            la[SLOT(j - 32)] = (u8)qa;
+          }
+        } else {
+          u64 P = KEY_NONE;
+          int pa = 0;
 #pragma unroll 8
-        for (int i = 0; i < 32; ++i) {
-          const u64 v = mine_ln[32 + i];
-          if (v < P) { P = v; pa = i; }
-          mine_ln[32 + i] = P;
-          mine_la[32 + i] = (u8)pa;
+          for (int i = 0; i < 32; ++i) {
+            const u64 v = ln[SLOT(i)];
+            if (v < P) { P = v; pa = i; }
+            ln[SLOT(i)] = P;
+            la[SLOT(i)] = (u8)pa;
+          }
         }
       }
     } else if (threadIdx.x < 64) {
       const u32 d = threadIdx.x >> 5;
-      u64* mine_ln = (d == 0 ? lh : lv)[lane];
-      u8* mine_la = (d == 0 ? ah : av)[lane];
-      if ((live_sh[d] >> lane) & 1u) {
-        line_bwd_arg<K>(mine_ln, mine_la);
-      } else {
-#pragma unroll 8
-        for (int x = 0; x < 32; ++x) {
-          mine_ln[32 + x] = KEY_NONE;
-          mine_la[32 + x] = ARG_NONE;
-        }
-      }
+      if ((d == 0 ? lhb : lvb) >> lane & 1u)
+        line_bwd_arg<K>((d == 0 ? lh : lv)[lane], (d == 0 ? ah : av)[lane]);
     }
     __syncthreads();
     // argmin code of every cell: offset d of the winning horizontal
     // candidate (0 .. K-1), 32 + d for a vertical one, ARG_NONE if no live
-    // candidate covers the cell; 8 cells per thread, one 8-byte store
+    // candidate covers the cell; 8 cells per thread, one 8-byte store.  Only
+    // live lines are read.
     bool any = false;
     u8* cdg = reinterpret_cast<u8*>(g.cmin) + (size_t)s * g.LL;
     {
       const u32 y = threadIdx.x >> 2, c0 = (threadIdx.x & 3) * 8;
-      u64 pack = 0;
+      const bool hl = (lhb >> y) & 1u;
+      const u32 vm = (lvb >> c0) & 0xFFu;
+      u64 pack = ~0ull;
+      if (hl || vm) {
+        pack = 0;
 #pragma unroll
-      for (u32 c = c0; c < c0 + 8; ++c) {
-        u64 vh = lh[y][32 + c], vv = lv[c][32 + y];
-        u32 dh, dv;
-        if (K == 32) {
-          // window of cell c on row y: Q[c+1] (previous block) vs P[c]
-          dh = c - ah[y][32 + c];
-          if (c < 31) {
-            const u64 q = lh[y][c + 1];
-            if (q < vh) { vh = q; dh = c + 32 - ah[y][c + 1]; }
+        for (u32 c = c0; c < c0 + 8; ++c) {
+          u64 vh = KEY_NONE, vv = KEY_NONE;
+          u32 dh = 0, dv = 0;
+          if (hl) {
+            vh = lh[y][SLOT(c)];
+            if constexpr (K == 32) {
+              // window of cell c on row y: Q at position c+1-32 vs P[c]
+              dh = c - ah[y][SLOT(c)];
+              if (c < 31) {
+                const u64 q = lh[y][SLOT((int)c - 31)];
+                if (q < vh) { vh = q; dh = c + 32 - ah[y][SLOT((int)c - 31)]; }
+              }
+            } else {
+              dh = ah[y][SLOT(c)];
+            }
           }
-          dv = y - av[c][32 + y];
-          if (y < 31) {
-            const u64 q = lv[c][y + 1];
-            if (q < vv) { vv = q; dv = y + 32 - av[c][y + 1]; }
+          if ((vm >> (c - c0)) & 1u) {
+            vv = lv[c][SLOT(y)];
+            if constexpr (K == 32) {
+              dv = y - av[c][SLOT(y)];
+              if (y < 31) {
+                const u64 q = lv[c][SLOT((int)y - 31)];
+                if (q < vv) { vv = q; dv = y + 32 - av[c][SLOT((int)y - 31)]; }
+              }
+            } else {
+              dv = av[c][SLOT(y)];
+            }
           }
-        } else {
-          dh = ah[y][32 + c];
-          dv = av[c][32 + y];
+          u32 code = ARG_NONE;
+          if (vh < vv) code = dh;
+          else if (vv < vh) code = 32u + dv;
+          pack |= (u64)code << (8 * (c - c0));
+          any |= code != ARG_NONE;
         }
-        u32 code = ARG_NONE;
-        if (vh < vv) code = dh;
-        else if (vv < vh) code = 32u + dv;
-        pack |= (u64)code << (8 * (c - c0));
-        any |= code != ARG_NONE;
       }
       *reinterpret_cast<u64*>(cdg + (size_t)(Y + y) * L + X + c0) = pack;
     }
     const bool tile_live = __syncthreads_or(any);
-    keyed = __reduce_add_sync(FULL, keyed);
-    if (lane == 0 && keyed) atomicAdd(g.work + 1, (u64)keyed);
     if (threadIdx.x == 0) {
       atomicAdd(g.work + 0, 1024ull);
       if (!tile_live) *dflag = 1;
