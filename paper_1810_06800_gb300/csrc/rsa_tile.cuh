@@ -146,42 +146,6 @@ struct ItemIter {
   }
 };
 
-// Accept one candidate with the whole warp (k <= 32): lane i writes cell i.
-// idx and key are warp-uniform.
-__device__ __forceinline__ void accept_warp(const Group& g, u32* occw, u32 T, u32 s, u32 idx,
-                                            u64 key) {
-  const u32 lane = threadIdx.x & 31;
-  SampleState& st = g.st[s];
-  u32 node = 0;
-  if (lane == 0) node = atomicAdd(&st.n_nodes, 1u);
-  node = __shfl_sync(FULL, node, 0);
-  if (node >= g.cap_nodes) {
-    if (lane == 0) atomicOr(&st.status, ST_NODE_OVF);
-    return;
-  }
-  const u32 L = g.L, k = g.k;
-  const u32 o = idx / (u32)g.LL, r = idx - o * (u32)g.LL;
-  const u32 y0 = r / L, x0 = r - y0 * L;
-  if (lane == 0) {
-    g.node_key[(size_t)s * g.cap_nodes + node] = key;
-    g.node_idx[(size_t)s * g.cap_nodes + node] = idx;
-    g.node_pos[(size_t)s * g.cap_nodes + node] = (o << 31) | (y0 << 15) | x0;
-  }
-  u32* ow = occw + (size_t)s * L * T;
-  u32* own = g.owner + (size_t)s * g.LL;
-  if (o == 0) {
-    const u32 b = x0 & 31u, w = x0 >> 5;
-    const u64 m = (k >= 64 ? ~0ull : ((1ull << k) - 1ull)) << b;
-    if (lane == 0) atomicOr(ow + (size_t)y0 * T + w, (u32)m);
-    if (lane == 1 && (m >> 32)) atomicOr(ow + (size_t)y0 * T + (w + 1 == T ? 0 : w + 1), (u32)(m >> 32));
-    if (lane < k) own[(size_t)y0 * L + wrap_lo((int)(x0 + lane), L)] = node;
-  } else if (lane < k) {
-    const u32 y = wrap_lo((int)(y0 + lane), L);
-    atomicOr(ow + (size_t)y * T + (x0 >> 5), 1u << (x0 & 31u));
-    own[(size_t)y * L + x0] = node;
-  }
-}
-
 constexpr u32 TILE_THREADS = 128;
 
 // Pass 1 of a round.  128 threads per tile, persistent over (sample, tile):
@@ -480,7 +444,11 @@ __global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
 // INC(x .. x+K-2).  No priority is needed except for the accepted ones.
 //  (a) stage the codes of the tile, the tile to the right (rows) and the
 //      tile below (columns); a dead neighbour reads as ARG_NONE;
-//  (b) warps 0-1 take 16 rows each, warps 2-3 16 columns each.
+//  (b) warps 0-1 take 16 rows each, warps 2-3 16 columns each; the accepted
+//      candidates of a line (disjoint k-mers) get consecutive nodes from one
+//      atomic, each accepting lane records its own node, the union of their
+//      cells is OR-ed into the occupancy words once per line, and the owner
+//      ids of each accepted k-mer's cells are one warp-wide store.
 template <int K>
 __global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg tc, u32* occw,
                                                               const u8* dead) {
@@ -527,6 +495,10 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg t
     const bool caller = g.keys != nullptr;
     constexpr u64 KM1 = K > 1 ? ((1ull << (K - 1)) - 1ull) : 0ull;  // INC bits a window needs
     const u32 l0 = half * 16;
+    SampleState& st = g.st[s];
+    u32* ows = occw + (size_t)s * L * T;
+    u32* own = g.owner + (size_t)s * g.LL;
+    const size_t nbase = (size_t)s * g.cap_nodes;
     u32 accepted = 0;
     for (u32 line = l0; line < l0 + 16; ++line) {
       u32 c0, c1, c2, c3;
@@ -548,16 +520,51 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg t
       const u64 inc = (u64)__ballot_sync(FULL, c0 >= base && c0 < top && c1 == c0 + 1) |
                       ((u64)__ballot_sync(FULL, c2 >= base && c2 < top && c3 == c2 + 1) << 32);
       const bool acc = ((S >> lane) & 1u) && ((inc >> lane) & KM1) == KM1;
-      u32 m = __ballot_sync(FULL, acc);
-      while (m) {
-        const u32 src = __ffs(m) - 1;
-        m &= m - 1;
-        const u64 idx = dirw == 0 ? (u64)(Y + line) * L + X + src
-                                  : g.LL + (u64)(Y + src) * L + X + line;
-        const u64 key = caller ? g.keys[idx] : mix64(zb + SM_GAMMA * idx);
-        accept_warp(g, occw, T, s, (u32)idx, key);
-        ++accepted;
+      const u32 m = __ballot_sync(FULL, acc);
+      if (!m) continue;
+      // nodes for the line's accepted candidates (disjoint k-mers), in lane
+      // order from one atomic; each accepting lane records its own
+      u32 nb = 0;
+      if (lane == 0) nb = atomicAdd(&st.n_nodes, (u32)__popc(m));
+      nb = __shfl_sync(FULL, nb, 0);
+      if (acc) {
+        const u32 node = nb + __popc(m & ((1u << lane) - 1u));
+        const u32 y0 = dirw == 0 ? Y + line : Y + lane, x0 = dirw == 0 ? X + lane : X + line;
+        const u64 idx = (u64)dirw * g.LL + (u64)y0 * L + x0;
+        if (node < g.cap_nodes) {
+          g.node_key[nbase + node] = caller ? g.keys[idx] : mix64(zb + SM_GAMMA * idx);
+          g.node_idx[nbase + node] = (u32)idx;
+          g.node_pos[nbase + node] = (dirw << 31) | (y0 << 15) | x0;
+        } else {
+          atomicOr(&st.status, ST_NODE_OVF);
+        }
       }
+      // occupancy: the union of their cells along the line, positions
+      // 0 .. 63 from the tile's first row / column, OR-ed in once
+      u64 cov = 0;
+      for (u32 mm = m; mm; mm &= mm - 1) cov |= kmask<K>() << (__ffs(mm) - 1);
+      if (dirw == 0) {
+        u32* w = ows + (size_t)(Y + line) * T;
+        if (lane == 0) atomicOr(w + tx, (u32)cov);
+        if (lane == 1 && (cov >> 32)) atomicOr(w + txr, (u32)(cov >> 32));
+      } else {
+        const u32 bit = 1u << line;  // column X + line is bit `line` of word tx
+        if ((cov >> lane) & 1u) atomicOr(ows + (size_t)(Y + lane) * T + tx, bit);
+        if ((cov >> (32 + lane)) & 1u) atomicOr(ows + (size_t)(tyb * 32 + lane) * T + tx, bit);
+      }
+      // owner ids: one warp-wide store per accepted k-mer (a row run, or a
+      // column run whose neighbours the same pass writes soon after)
+      for (u32 mm = m; mm; mm &= mm - 1) {
+        const u32 src = __ffs(mm) - 1;
+        const u32 node = nb + __popc(m & ((1u << src) - 1u));
+        if (node < g.cap_nodes && lane < (u32)K) {
+          if (dirw == 0)
+            own[(size_t)(Y + line) * L + wrap_lo((int)(X + src + lane), L)] = node;
+          else
+            own[(size_t)wrap_lo((int)(Y + src + lane), L) * L + X + line] = node;
+        }
+      }
+      accepted += __popc(m);
     }
     if (lane == 0 && accepted) atomicAdd(g.work + 3, (u64)accepted);
     if (threadIdx.x == 0) atomicAdd(g.work + 2, 1024ull);
