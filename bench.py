@@ -40,7 +40,13 @@ METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
 # line path): bytes per lattice cell per launch -- the cell-minimum passes
 # read occupancy (1 B) and write or read-modify-write the 8-byte cell
 # minimum, the acceptance passes read it.
-BYTES_PER_CELL = {"k_row_cmin": 9, "k_col_cmin": 17, "k_row_accept": 8, "k_col_accept": 8}
+BYTES_PER_CELL = {"k_row_cmin": 9, "k_col_cmin": 17, "k_row_accept": 8, "k_col_accept": 8,
+                  # long-k line path: window minima write the 8-byte minimum of
+                  # one orientation and read occupancy bits; the combine reads
+                  # both minima and writes two 2-byte argmin codes; acceptance
+                  # reads one code per cell and occupancy bits
+                  "k_line_cmin_h": 8.125, "k_line_cmin_v": 8.125, "k_line_codes": 20,
+                  "k_line_accept_h": 2.125, "k_line_accept_v": 2.125}
 # Integer-ALU kernels (the 32x32 tile path), counted in 32-bit lane
 # operations: a 64-bit minimum is 4 ops (two compares, two selects) plus 1
 # when the argmin is tracked, a width-k window minimum by van Herk /
@@ -62,13 +68,21 @@ TILE_WORK = {"k_tile_cmin": ("cmin_cells", "cmin_keys"),
 ALU_LANES_PER_SM = 128  # 4 schedulers x 32 lanes, one integer op per lane per clock
 
 
-def src_digest() -> str:
-    h = hashlib.sha256()
-    d = os.path.join(ROOT, "paper_1810_06800_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
-    return h.hexdigest()[:16]
+# The source file that holds each kernel: a DRAM-traffic figure measured by
+# ncu is used only while that file is unchanged.
+KERNEL_FILE = {"k_tile_cmin": "rsa_tile.cuh", "k_tile_accept": "rsa_tile.cuh",
+               "k_line_cmin_h": "rsa_line.cuh", "k_line_cmin_v": "rsa_line.cuh",
+               "k_line_codes": "rsa_line.cuh", "k_line_accept_h": "rsa_line.cuh",
+               "k_line_accept_v": "rsa_line.cuh", "k_row_cmin": "rsa_kernels.cuh",
+               "k_col_cmin": "rsa_kernels.cuh", "k_row_accept": "rsa_kernels.cuh",
+               "k_col_accept": "rsa_kernels.cuh"}
+
+
+def src_digest(kernel: str) -> str:
+    """First 16 hex digits of the SHA-256 of the file that holds `kernel`."""
+    f = os.path.join(ROOT, "paper_1810_06800_gb300", "csrc", KERNEL_FILE.get(kernel, "rsa.cu"))
+    with open(f, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def measured_peaks():
@@ -322,7 +336,7 @@ def main():
         with open(tp) as f:
             traffic_db = json.load(f)
     ent = traffic_db.get(dom)
-    fresh = bool(ent) and ent.get("src") == src_digest()
+    fresh = bool(ent) and ent.get("src") == src_digest(dom)
     if dom in TILE_WORK:
         cells_key, keys_key = TILE_WORK[dom]
         cells, keys = work[cells_key], work[keys_key]
