@@ -33,6 +33,7 @@ constexpr u64 KEY_NONE = 0xFFFFFFFFFFFFFFFFull;  // dead / no candidate
 constexpr u64 SM_GAMMA = 0x9E3779B97F4A7C15ull;  // splitmix64 increment
 constexpr u32 NONE32 = 0xFFFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr u32 OWN_V = 1u << 31;  // owner word: set for a vertical k-mer's cells
 constexpr u32 NBKT = 256;  // time buckets (top 8 bits of a priority)
 
 // status bits (per sample), mapped to RSA_E* codes by the host
@@ -89,7 +90,7 @@ struct Group {         // one batch of samples sharing (L, k)
   u32 cap_nodes, cap_edges;
   u64 LL;
   u8* occ;             // [n][L][L]   1 = occupied
-  u32* owner;          // [n][L][L]   node id or NONE32
+  u32* owner;          // [n][L][L]   node id (| OWN_V if vertical) or NONE32
   u64* cmin;           // [n][L][L]   per-cell minimum of live priorities
   u64* base;           // [n]         splitmix64 stream base per sample
   const u64* keys;     // caller priorities [2 L^2] (test path), else null
@@ -270,14 +271,14 @@ __device__ __forceinline__ void accept_candidate(const Group& g, u32 s, u32 idx,
     u32 x = x0;
     for (u32 i = 0; i < g.k; ++i) {
       occ[(size_t)y0 * L + x] = 1;
-      own[(size_t)y0 * L + x] = node;
+      own[(size_t)y0 * L + x] = node;  // horizontal: bit 31 clear
       if (++x == L) x = 0;
     }
   } else {
     u32 y = y0;
     for (u32 i = 0; i < g.k; ++i) {
       occ[(size_t)y * L + x0] = 1;
-      own[(size_t)y * L + x0] = node;
+      own[(size_t)y * L + x0] = node | OWN_V;
       if (++y == L) y = 0;
     }
   }

@@ -276,11 +276,8 @@ __global__ void k_edges(Group g) {
       u32 kind = 3;  // contact class: 0 both horizontal, 1 both vertical, 2 mixed
       if (a != NONE32) {
         b = own[(size_t)by * L + bx];
-        if (b != NONE32 && b != a) {
-          const u32* npos = g.node_pos + (size_t)s * g.cap_nodes;
-          const u32 oa = npos[a] >> 31, ob = npos[b] >> 31;
-          kind = oa != ob ? 2u : oa;
-        }
+        // owner words carry the k-mer's orientation in bit 31
+        if (b != NONE32 && b != a) kind = (a ^ b) >> 31 ? 2u : a >> 31;
         if (b != NONE32) {
           bool internal = false;
           // the previous contact of the run: one row up (+x edges) or one
@@ -292,11 +289,12 @@ __global__ void k_edges(Group g) {
           const u32 pb = force ? NONE32 : own[(size_t)qy * L + qx];
           const bool same_pair = pa == a && pb == b;
           if (!same_pair || full_compare) {
-            d = contact_delta(g, s, y, x, by, bx, dir, a, b, &internal);
+            d = contact_delta(g, s, y, x, by, bx, dir, a & ~OWN_V, b & ~OWN_V, &internal);
             emit = !internal;
             if (emit && same_pair) {
               bool pint = false;
-              const u32 pd = contact_delta(g, s, py, px, qy, qx, dir, pa, pb, &pint);
+              const u32 pd = contact_delta(g, s, py, px, qy, qx, dir, pa & ~OWN_V, pb & ~OWN_V,
+                                           &pint);
               emit = pd != d;
             }
           }
@@ -317,9 +315,10 @@ __global__ void k_edges(Group g) {
         const u32 e = basei + __popc(mask & ((1u << lane) - 1u));
         if (e < g.cap_edges) {
           Edge ed;
-          ed.time = max(nkey[a], nkey[b]);
-          ed.m1 = a;
-          ed.m2 = b;
+          const u32 ma = a & ~OWN_V, mb = b & ~OWN_V;
+          ed.time = max(nkey[ma], nkey[mb]);
+          ed.m1 = ma;
+          ed.m2 = mb;
           ed.dxy = d;
           ed.pad = 0;
           E[e] = ed;
@@ -377,12 +376,16 @@ __global__ void __launch_bounds__(1024) k_bucket(Group g) {
 }
 
 // ---------------------------------------------------------------------
-// First wrap by bisection over the accepted priorities (Sec. II.D).
-// wrap(T): does the graph of k-mers with key <= T contain a cycle of
-// non-zero winding?  It is monotone in T; n_c = #{keys <= T*} for the
-// smallest such accepted key T*.  Each probe starts from the union-find
-// state of the last non-wrapping threshold `lo` and adds only edges with
-// lo < time <= mid.  Union-find words: parent (bits 0-31) and the lifted
+// First wrap by bisection over the number of placed k-mers (Sec. II.D).
+// wrap(m): does the graph of the first m accepted k-mers (the m smallest
+// keys) contain a cycle of non-zero winding?  It is monotone in m, and n_c
+// is the smallest m with wrap(m).  The first probe takes every k-mer (the
+// jammed lattice must wrap); later probes bisect the rank interval
+// (cnt_lo, cnt_hi] and take mid = T_r, the key of rank r, so that the edges
+// of a probe are those with time (the larger key of their two ends) <= T_r.
+// Each probe starts from the union-find state of the last non-wrapping rank
+// cnt_lo (threshold `lo`) and adds only edges with lo < time <= mid, so the
+// probes after the first non-wrapping one touch a halving share of edges.  Union-find words: parent (bits 0-31) and the lifted
 // offset of the node from its parent, dx (32-47), dy (48-63), modulo 2^16.
 // A wrap is a cycle of primitive winding (a, b) times L; for L < 65536 its
 // offset is never 0 modulo 2^16, so 16-bit offsets decide exactly.
@@ -464,6 +467,7 @@ __global__ void k_search_init(Group g) {
   st.hi = KEY_NONE;
   st.cnt_hi = min(st.n_nodes, g.cap_nodes);
   st.mid = KEY_NONE;  // first probe: the whole jammed lattice must wrap
+  st.cnt_mid = st.cnt_hi;
   st.hi_ok = 0;
   st.cur = 0;
   st.sdone = (st.status & (ST_NODE_OVF | ST_EDGE_OVF | ST_ROUND_CAP)) ? 1u : 0u;
@@ -484,10 +488,7 @@ __global__ void k_probe_copy(Group g) {
   const u32 s = blockIdx.y;
   SampleState& st = g.st[s];
   if (st.sdone) return;
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    st.wrap = 0;
-    st.cnt_mid = 0;
-  }
+  if (threadIdx.x == 0 && blockIdx.x == 0) st.wrap = 0;
   const u32 nn = min(st.n_nodes, g.cap_nodes);
   const u64* S = g.uf + ((size_t)s * 2 + st.cur) * g.cap_nodes;
   u64* Wd = g.uf + ((size_t)s * 2 + (st.cur ^ 1u)) * g.cap_nodes;
@@ -502,37 +503,69 @@ __global__ void k_probe(Group g) {
   const u64 lo = st.lo, mid = st.mid;
   const bool lo_valid = st.lo_valid != 0;
   const u32* eb = g.ebkt + (size_t)s * (NBKT + 1);
-  const u32* nb = g.nbkt + (size_t)s * (NBKT + 1);
   const u32 blo = lo_valid ? (u32)(lo >> 56) : 0u, bmid = (u32)(mid >> 56);
   const u32 e0 = eb[blo], e1 = eb[bmid + 1];
-  const u32 n0 = nb[bmid], n1 = nb[bmid + 1];
   u64* Wd = g.uf + ((size_t)s * 2 + (st.cur ^ 1u)) * g.cap_nodes;
   const Edge* E = g.edges_b + (size_t)s * g.cap_edges;
-  const u64* nkey = g.nkey_b + (size_t)s * g.cap_nodes;
   bool wrap = false, capped = false;
-  u32 cnt = 0;
   const u32 stride = gridDim.x * blockDim.x;
   for (u32 i = e0 + blockIdx.x * blockDim.x + threadIdx.x; i < e1; i += stride) {
     const Edge e = E[i];
     if (e.time > mid || (lo_valid && e.time <= lo)) continue;
     if (uf_union(Wd, e.m1, e.m2, e.dxy, &capped)) wrap = true;
   }
-  for (u32 i = n0 + blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += stride)
-    cnt += nkey[i] <= mid;
-  // block reductions
   const bool bw = __syncthreads_or(wrap);
   const bool bc = __syncthreads_or(capped);
-  cnt = __reduce_add_sync(FULL, cnt);
-  __shared__ u32 part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
-  __syncthreads();
   if (threadIdx.x == 0) {
-    u32 t = blockIdx.x == 0 ? n0 : 0u;  // all nodes of the buckets below mid's
-    for (u32 w = 0; w < (blockDim.x + 31) / 32; ++w) t += part[w];
-    if (t) atomicAdd(&st.cnt_mid, t);
     if (bw) atomicOr(&st.wrap, 1u);
     if (bc) atomicOr(&st.status, ST_UF_CAP);
   }
+}
+
+// mid := the key of rank cnt_mid (1-based) among the sample's node keys.
+// The keys are grouped by their top byte (k_bucket); the rank's bucket is
+// found from the bucket offsets and the key inside it by an 8-bit radix
+// select over the remaining 56 bits.  One block per sample.
+__global__ void __launch_bounds__(256) k_select_mid(Group g) {
+  __shared__ u32 hist[256];
+  __shared__ u32 bk_sh, rank_sh;
+  __shared__ u64 pre_sh;
+  const u32 s = blockIdx.x;
+  SampleState& st = g.st[s];
+  if (st.sdone) return;
+  const u32* nb = g.nbkt + (size_t)s * (NBKT + 1);
+  const u64* K = g.nkey_b + (size_t)s * g.cap_nodes;
+  const u32 r = st.cnt_mid;
+  if (threadIdx.x == 0) bk_sh = 0;
+  __syncthreads();
+  for (u32 b = threadIdx.x; b < NBKT; b += blockDim.x)
+    if (nb[b] < r && r <= nb[b + 1]) bk_sh = b;
+  __syncthreads();
+  const u32 nn = min(st.n_nodes, g.cap_nodes);
+  const u32 bk = bk_sh, k0 = min(nb[bk], nn), k1 = min(nb[bk + 1], nn);
+  u64 pre = (u64)bk << 56, mask = 0xFFull << 56;
+  u32 rank = r - k0;
+  for (int shift = 48; shift >= 0; shift -= 8) {
+    for (u32 i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (u32 i = k0 + threadIdx.x; i < k1; i += blockDim.x) {
+      const u64 kk = K[i];
+      if ((kk & mask) == pre) atomicAdd(&hist[(u32)(kk >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      u32 d = 0, below = 0;
+      while (d < 255 && below + hist[d] < rank) below += hist[d++];
+      rank_sh = rank - below;
+      pre_sh = pre | ((u64)d << shift);
+    }
+    __syncthreads();
+    rank = rank_sh;
+    pre = pre_sh;
+    mask |= 255ull << shift;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st.mid = pre;
 }
 
 __global__ void k_search_decide(Group g, u32 probe_cap, u32* n_open) {
@@ -579,7 +612,8 @@ __global__ void k_search_decide(Group g, u32 probe_cap, u32* n_open) {
     st.sdone = 1;
     return;
   }
-  st.mid = st.lo_valid ? st.lo + (st.hi - st.lo) / 2 : st.hi / 2;
+  // next rank, strictly inside (cnt_lo, cnt_hi); k_select_mid sets its key
+  st.cnt_mid = st.cnt_lo + (st.cnt_hi - st.cnt_lo) / 2;
   atomicAdd(n_open, 1u);
 }
 

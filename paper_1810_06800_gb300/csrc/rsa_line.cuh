@@ -353,7 +353,7 @@ __device__ void accept_block(const Group& g, u32* occw, u32* occT, u32 T, u32 s,
     else { y += i; if (y >= L) y -= L; }
     atomicOr(ow + (size_t)y * T + (x >> 5), 1u << (x & 31u));
     atomicOr(ot + (size_t)x * T + (y >> 5), 1u << (y & 31u));
-    own[(size_t)y * L + x] = node;
+    own[(size_t)y * L + x] = node | (o << 31);
   }
 }
 

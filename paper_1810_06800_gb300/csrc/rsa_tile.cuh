@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg t
           if (dirw == 0)
             own[(size_t)(Y + line) * L + wrap_lo((int)(X + src + lane), L)] = node;
           else
-            own[(size_t)wrap_lo((int)(Y + src + lane), L) * L + X + line] = node;
+            own[(size_t)wrap_lo((int)(Y + src + lane), L) * L + X + line] = node | OWN_V;
         }
       }
       accepted += __popc(m);

@@ -81,9 +81,13 @@ class Scheduler:
             t.start()
 
     def batch_size(self, L: int, k: int, n: int) -> int:
-        """Largest batch (<= max_batch, <= n) whose workspace fits the budget."""
+        """Largest batch (<= max_batch, <= n) whose workspace fits a worker's
+        share of the budget (budget / workers, so that every worker can hold a
+        batch at once and no single allocation claims all free HBM); a batch
+        of one sample may use the whole budget."""
+        share = max(1, self.budget // max(1, len(self.threads)))
         b = min(n, self.max_batch)
-        while b > 1 and self.ws_bytes(L, k, b) > self.budget:
+        while b > 1 and self.ws_bytes(L, k, b) > share:
             b = (b + 1) // 2
         if self.ws_bytes(L, k, b) > self.budget:
             raise MemoryError(f"one sample of L={L} k={k} needs {self.ws_bytes(L, k, 1)} bytes, "
@@ -198,7 +202,13 @@ class GpuRunner:
             h = self.handles[w].get((L, k))
             if h is None:
                 h = self.handles[w][(L, k)] = rsa.rsa_create(L, k, 1)
-            buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+            try:
+                buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+            except torch.cuda.OutOfMemoryError:
+                # the free budget counted memory that torch's cache holds in
+                # blocks too small for this workspace: return them and retry
+                torch.cuda.empty_cache()
+                buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
             ptr = (buf.data_ptr() + 255) // 256 * 256
             try:
                 rsa.rsa_bind_workspace(h, ptr, nbytes)

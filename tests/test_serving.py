@@ -59,6 +59,16 @@ def test_scheduler_splits_batches_and_respects_the_budget():
     assert st["peak_concurrent_batches"] >= 2
 
 
+def test_batches_fit_a_workers_share_of_the_budget():
+    # 4 workers share an 8 MiB budget: a batch takes at most 2 MiB, so every
+    # worker can hold one at once; a single sample may still use it all
+    sch = serve.Scheduler(lambda *a: None, _fake_ws, budget_bytes=8 * 1024 * 1024, workers=4,
+                          max_batch=256)
+    assert sch.batch_size(1024, 32, 100) == 2
+    assert sch.batch_size(2048, 32, 100) == 1
+    sch.close()
+
+
 def test_batch_size_shrinks_to_fit_the_budget():
     sch = serve.Scheduler(lambda *a: None, _fake_ws, budget_bytes=1024 * 1024 * 3, workers=1,
                           max_batch=256)
