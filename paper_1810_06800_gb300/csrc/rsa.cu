@@ -204,14 +204,13 @@ enum Kind {
   KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
   KD_LINE_CMIN_H, KD_LINE_CMIN_V, KD_LINE_COMBINE, KD_LINE_ACCEPT_H, KD_LINE_ACCEPT_V,
   KD_LINE_CODES,
-  KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE,
-  KD_SELECT, KD_COUNT
+  KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE, KD_COUNT
 };
 const char* const kKindNames[KD_COUNT] = {
     "k_init",         "k_row_cmin",    "k_col_cmin",   "k_row_accept", "k_col_accept",
     "k_tile_cmin",    "k_tile_accept", "k_line_cmin_h", "k_line_cmin_v", "k_line_combine",
     "k_line_accept_h", "k_line_accept_v", "k_line_codes", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
-    "k_probe_copy",   "k_probe",       "k_search_decide", "k_select_mid"};
+    "k_probe_copy",   "k_probe",       "k_search_decide"};
 
 // Optional per-kernel timing with CUDA events recorded around each launch
 // on the launch stream, plus launch counts (always kept).
@@ -602,9 +601,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
       if (cudaMemsetAsync(d_counter + 1, 0, 4, st) != cudaSuccess) body_rc = RSA_ECUDA;
       launch(h, KD_PROBE_COPY, k_probe_copy, dim3(copy_bx, n), dim3(256), 0, st, g);
       launch(h, KD_PROBE, k_probe, dim3(probe_bx, n), dim3(256), 0, st, g);
-      launch(h, KD_DECIDE, k_search_decide, dim3((n + 127) / 128), dim3(128), 0, st, g,
-             (u32)PROBE_CAP, d_counter + 1);
-      launch(h, KD_SELECT, k_select_mid, dim3(n), dim3(256), 0, st, g);
+      launch(h, KD_DECIDE, k_search_decide, dim3(n), dim3(256), 0, st, g, (u32)PROBE_CAP,
+             d_counter + 1);
     }
   };
   for (u32 chunks = 0; chunks * PROBE_CHECK < PROBE_CAP + PROBE_CHECK;) {

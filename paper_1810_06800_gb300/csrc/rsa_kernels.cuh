@@ -522,26 +522,70 @@ __global__ void k_probe(Group g) {
   }
 }
 
-// mid := the key of rank cnt_mid (1-based) among the sample's node keys.
-// The keys are grouped by their top byte (k_bucket); the rank's bucket is
-// found from the bucket offsets and the key inside it by an 8-bit radix
-// select over the remaining 56 bits.  One block per sample.
-__global__ void __launch_bounds__(256) k_select_mid(Group g) {
+// One bisection step of sample s (one thread): read the probe's wrap flag,
+// move lo or hi, finish or pick the next rank.  True if another probe follows.
+__device__ bool search_step(Group& g, SampleState& st, u32 probe_cap, u32* n_open) {
+  st.probes += 1;
+  if (st.status & ST_UF_CAP) {
+    st.sdone = 1;
+    return false;
+  }
+  const bool w = st.wrap != 0;
+  if (!st.hi_ok) {
+    if (!w) {
+      st.status |= ST_NOWRAP;
+      st.nc = NONE32;
+      st.sdone = 1;
+      return false;
+    }
+    st.hi_ok = 1;
+    st.cnt_hi = st.cnt_mid;
+  } else if (w) {
+    st.hi = st.mid;
+    st.cnt_hi = st.cnt_mid;
+  } else {
+    st.lo = st.mid;
+    st.lo_valid = 1;
+    st.cnt_lo = st.cnt_mid;
+    st.cur ^= 1u;
+  }
+  if (st.cnt_hi <= st.cnt_lo) {
+    st.status |= ST_SEARCH_BAD;
+    st.sdone = 1;
+    return false;
+  }
+  if (st.cnt_hi - st.cnt_lo == 1) {
+    st.nc = st.cnt_hi;
+    st.sdone = 1;
+    return false;
+  }
+  if (st.probes >= probe_cap) {
+    st.status |= ST_SEARCH_CAP;
+    st.sdone = 1;
+    return false;
+  }
+  // next rank, strictly inside (cnt_lo, cnt_hi)
+  st.cnt_mid = st.cnt_lo + (st.cnt_hi - st.cnt_lo) / 2;
+  atomicAdd(n_open, 1u);
+  return true;
+}
+
+// mid := the key of rank r (1-based) among the sample's node keys, by the
+// whole block.  The keys are grouped by their top byte (k_bucket); the rank's
+// bucket is found from the bucket offsets and the key inside it by an 8-bit
+// radix select over the remaining 56 bits.
+__device__ u64 select_rank(const Group& g, u32 s, u32 r) {
   __shared__ u32 hist[256];
   __shared__ u32 bk_sh, rank_sh;
   __shared__ u64 pre_sh;
-  const u32 s = blockIdx.x;
-  SampleState& st = g.st[s];
-  if (st.sdone) return;
   const u32* nb = g.nbkt + (size_t)s * (NBKT + 1);
   const u64* K = g.nkey_b + (size_t)s * g.cap_nodes;
-  const u32 r = st.cnt_mid;
   if (threadIdx.x == 0) bk_sh = 0;
   __syncthreads();
   for (u32 b = threadIdx.x; b < NBKT; b += blockDim.x)
     if (nb[b] < r && r <= nb[b + 1]) bk_sh = b;
   __syncthreads();
-  const u32 nn = min(st.n_nodes, g.cap_nodes);
+  const u32 nn = min(g.st[s].n_nodes, g.cap_nodes);
   const u32 bk = bk_sh, k0 = min(nb[bk], nn), k1 = min(nb[bk + 1], nn);
   u64 pre = (u64)bk << 56, mask = 0xFFull << 56;
   u32 rank = r - k0;
@@ -565,56 +609,21 @@ __global__ void __launch_bounds__(256) k_select_mid(Group g) {
     mask |= 255ull << shift;
     __syncthreads();
   }
-  if (threadIdx.x == 0) st.mid = pre;
+  return pre;
 }
 
-__global__ void k_search_decide(Group g, u32 probe_cap, u32* n_open) {
-  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.n) return;
+// After a probe: one block per sample takes the bisection step and, if the
+// search goes on, selects the key of the next rank as the next threshold.
+__global__ void __launch_bounds__(256) k_search_decide(Group g, u32 probe_cap, u32* n_open) {
+  __shared__ u32 go;
+  const u32 s = blockIdx.x;
   SampleState& st = g.st[s];
   if (st.sdone) return;
-  st.probes += 1;
-  if (st.status & ST_UF_CAP) {
-    st.sdone = 1;
-    return;
-  }
-  const bool w = st.wrap != 0;
-  if (!st.hi_ok) {
-    if (!w) {
-      st.status |= ST_NOWRAP;
-      st.nc = NONE32;
-      st.sdone = 1;
-      return;
-    }
-    st.hi_ok = 1;
-    st.cnt_hi = st.cnt_mid;
-  } else if (w) {
-    st.hi = st.mid;
-    st.cnt_hi = st.cnt_mid;
-  } else {
-    st.lo = st.mid;
-    st.lo_valid = 1;
-    st.cnt_lo = st.cnt_mid;
-    st.cur ^= 1u;
-  }
-  if (st.cnt_hi <= st.cnt_lo) {
-    st.status |= ST_SEARCH_BAD;
-    st.sdone = 1;
-    return;
-  }
-  if (st.cnt_hi - st.cnt_lo == 1) {
-    st.nc = st.cnt_hi;
-    st.sdone = 1;
-    return;
-  }
-  if (st.probes >= probe_cap) {
-    st.status |= ST_SEARCH_CAP;
-    st.sdone = 1;
-    return;
-  }
-  // next rank, strictly inside (cnt_lo, cnt_hi); k_select_mid sets its key
-  st.cnt_mid = st.cnt_lo + (st.cnt_hi - st.cnt_lo) / 2;
-  atomicAdd(n_open, 1u);
+  if (threadIdx.x == 0) go = search_step(g, st, probe_cap, n_open) ? 1u : 0u;
+  __syncthreads();
+  if (!go) return;
+  const u64 mid = select_rank(g, s, st.cnt_mid);
+  if (threadIdx.x == 0) st.mid = mid;
 }
 
 }  // namespace rsak
