@@ -244,7 +244,9 @@ __device__ __forceinline__ u32 contact_delta(const Group& g, u32 s, u32 y, u32 x
   return ((u32)dx & 0xFFFFu) | (((u32)dy & 0xFFFFu) << 16);
 }
 
-__global__ void k_edges(Group g) {
+constexpr u32 EDGES_THREADS = 256;
+
+__global__ void __launch_bounds__(EDGES_THREADS) k_edges(Group g) {
   const u32 s = blockIdx.y;
   const u32 L = g.L;
   const u32 lane = threadIdx.x & 31;
@@ -267,7 +269,13 @@ __global__ void k_edges(Group g) {
     const u32 x = inb ? xx : 0;
     const u32 yp = y == 0 ? L - 1 : y - 1, yn = y + 1 == L ? 0 : y + 1;
     const u32 xp = x == 0 ? L - 1 : x - 1, xn = x + 1 == L ? 0 : x + 1;
-    const u32 a = inb ? own[(size_t)y * L + x] : NONE32;
+    // the cell, its +x / +y neighbours, and the cells whose contact precedes
+    // each of the two in its run (up, up-right for +x; left, down-left for
+    // +y): all loaded at once, so their latencies overlap
+    const u32 a = inb ? __ldg(own + (size_t)y * L + x) : NONE32;
+    const u32 o_r = __ldg(own + (size_t)y * L + xn), o_d = __ldg(own + (size_t)yn * L + x);
+    const u32 o_u = __ldg(own + (size_t)yp * L + x), o_ur = __ldg(own + (size_t)yp * L + xn);
+    const u32 o_l = __ldg(own + (size_t)y * L + xp), o_dl = __ldg(own + (size_t)yn * L + xp);
 #pragma unroll
     for (u32 dir = 0; dir < 2; ++dir) {
       const u32 by = dir ? yn : y, bx = dir ? x : xn;
@@ -275,7 +283,7 @@ __global__ void k_edges(Group g) {
       u32 b = NONE32, d = 0;
       u32 kind = 3;  // contact class: 0 both horizontal, 1 both vertical, 2 mixed
       if (a != NONE32) {
-        b = own[(size_t)by * L + bx];
+        b = dir ? o_d : o_r;
         // owner words carry the k-mer's orientation in bit 31
         if (b != NONE32 && b != a) kind = (a ^ b) >> 31 ? 2u : a >> 31;
         if (b != NONE32) {
@@ -285,8 +293,8 @@ __global__ void k_edges(Group g) {
           const bool force = dir == 0 ? (y == 0) : (x == 0);
           const u32 py = dir == 0 ? yp : y, px = dir == 0 ? x : xp;
           const u32 qy = dir == 0 ? yp : yn, qx = dir == 0 ? xn : xp;
-          const u32 pa = force ? NONE32 : own[(size_t)py * L + px];
-          const u32 pb = force ? NONE32 : own[(size_t)qy * L + qx];
+          const u32 pa = force ? NONE32 : (dir == 0 ? o_u : o_l);
+          const u32 pb = force ? NONE32 : (dir == 0 ? o_ur : o_dl);
           const bool same_pair = pa == a && pb == b;
           if (!same_pair || full_compare) {
             d = contact_delta(g, s, y, x, by, bx, dir, a & ~OWN_V, b & ~OWN_V, &internal);
