@@ -211,3 +211,15 @@ def test_full_size_properties(L, k, n):
     pj = k * nj / L**2
     assert abs(pj.mean() - (0.6575 if k == 4096 else 0.6618)) < 0.03
     lat.close()
+
+
+@pytest.mark.parametrize("L,k", [(64, 4), (1024, 32), (1024, 64)])
+def test_bisection_probes_are_logarithmic_in_n_j(L, k):
+    # the first-wrap search bisects the number of placed k-mers: one probe of
+    # the jammed lattice, then at most ceil(log2 n_j) halvings
+    lat = rsa.Lattice(L, k)
+    nj, nc = lat.run(list(range(1, 17)))
+    st = lat.stats(16)
+    for i in range(16):
+        assert st["probes"][i] <= 1 + int(np.ceil(np.log2(int(nj[i])))), (i, st["probes"][i], nj[i])
+    lat.close()
