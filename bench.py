@@ -34,6 +34,8 @@ WORKLOADS = {
     # small cases for ncu captures (a few GB on the device)
     "L1024_k32_x64": dict(L=1024, k=32, n=64),
     "L8192_k512_x2": dict(L=8192, k=512, n=2),
+    # large k held on the device: 8 samples of L = 32768 (1 G cells each)
+    "L32768_k4096_x8": dict(L=32768, k=4096, n=8),
 }
 METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
 # Algorithmic work of the round kernels.  Byte-type kernels (the general

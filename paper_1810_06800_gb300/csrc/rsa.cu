@@ -58,7 +58,7 @@ struct Geometry {
   bool tile;                    // power-of-two k <= 32 and L % 32 == 0
   bool line;                    // 32 <= k <= LINE_KMAX, L % 32 == 0, not tile
   LineCfg lc;
-  size_t line_smem, line_codes_smem;
+  size_t line_smem, line_acc_smem, line_codes_smem;
   TileCfg tc;                   // (items filled per run)
   RowCfg row;
   ColCfg col;
@@ -88,11 +88,20 @@ Geometry plan(u32 L, u32 k) {
     // so at least two blocks fit on an SM
     u32 S = std::min<u32>(L, 4096);
     while (S > 256 && line_smem_bytes(S + k - 1, S, k) > 100 * 1024) S -= 256;
+    // very long windows: if that cap leaves segments shorter than k, take
+    // S = k (rounded down to 32, at most L) with the one-array layout, which
+    // halves the bytes per value: fewer halo values per output cell
+    G.lc.compact = 0;
+    if (S < k) {
+      S = std::min<u32>(L, k & ~31u);
+      G.lc.compact = 1;
+    }
     G.lc.S = S;
     G.lc.nseg = (L + S - 1) / S;
     G.lc.nmax = S + k - 1;
     G.lc.T = L / 32;
-    G.line_smem = line_smem_bytes(G.lc.nmax, S, k);
+    G.line_smem = line_smem_bytes(G.lc.nmax, S, k, G.lc.compact != 0);
+    G.line_acc_smem = line_smem_bytes(G.lc.nmax, S, k);
     G.line_codes_smem = line_codes_smem_bytes(G.lc.nmax);
   }
   // ---- row pass: one warp per (row, segment) ----
@@ -498,8 +507,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   if (G.line) {
     if ((rc = set_smem(k_line_cmin<0>, G.line_smem))) return rc;
     if ((rc = set_smem(k_line_cmin<1>, G.line_smem))) return rc;
-    if ((rc = set_smem(k_line_accept<0>, G.line_smem))) return rc;
-    if ((rc = set_smem(k_line_accept<1>, G.line_smem))) return rc;
+    if ((rc = set_smem(k_line_accept<0>, G.line_acc_smem))) return rc;
+    if ((rc = set_smem(k_line_accept<1>, G.line_acc_smem))) return rc;
     if ((rc = set_smem(k_line_accept_codes<0>, G.line_codes_smem))) return rc;
     if ((rc = set_smem(k_line_accept_codes<1>, G.line_codes_smem))) return rc;
   } else if (!G.tile) {
@@ -541,9 +550,9 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
         if (h->with_keys) {
           // caller-supplied priorities cannot be inverted: compare values
           launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, st, g, g.cmin, cB);
-          launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_smem, st,
+          launch(h, KD_LINE_ACCEPT_H, k_line_accept<0>, lg, dim3(LINE_THREADS), G.line_acc_smem, st,
                  g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
-          launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_smem, st,
+          launch(h, KD_LINE_ACCEPT_V, k_line_accept<1>, lg, dim3(LINE_THREADS), G.line_acc_smem, st,
                  g, G.lc, occw, occT, (const u64*)g.cmin, (const u64*)cB);
         } else {
           u16* c16 = reinterpret_cast<u16*>(b + l.code16);

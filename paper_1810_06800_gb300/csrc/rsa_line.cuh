@@ -28,6 +28,7 @@ struct LineCfg {
   u32 nseg;     // segments per line
   u32 nmax;     // S + k - 1
   u32 T;        // words per line = L / 32
+  u32 compact;  // S <= k: the window-minimum pass keeps one value array (below)
 };
 
 // Segmented (k-aligned blocks) min-scan of n values held by the whole block.
@@ -174,14 +175,17 @@ struct LineSmem {
   u64* V; u64* Q; u32* w; u32* wpre; u32* scr; u32* acc; u64* wv; u32* wf;
 };
 __host__ __device__ inline u32 line_wn(u32 S, u32 k) { return (S + 2 * k + 64) / 32 + 3; }
-__host__ __device__ inline size_t line_smem_bytes(u32 nmax, u32 S, u32 k) {
-  return (size_t)nmax * 16 + (size_t)line_wn(S, k) * 8 + 64 * 4 + LINE_ACC * 4 + 32 * 8 + 32 * 4;
+// compact: one value array (Q aliases V), see k_line_cmin.
+__host__ __device__ inline size_t line_smem_bytes(u32 nmax, u32 S, u32 k, bool compact = false) {
+  return (size_t)nmax * (compact ? 8 : 16) + (size_t)line_wn(S, k) * 8 + 64 * 4 + LINE_ACC * 4 +
+         32 * 8 + 32 * 4;
 }
-__device__ inline LineSmem line_smem(unsigned char* raw, u32 nmax, u32 S, u32 k) {
+__device__ inline LineSmem line_smem(unsigned char* raw, u32 nmax, u32 S, u32 k,
+                                     bool compact = false) {
   LineSmem m;
   m.V = reinterpret_cast<u64*>(raw);
-  m.Q = m.V + nmax;
-  m.w = reinterpret_cast<u32*>(m.Q + nmax);
+  m.Q = compact ? m.V : m.V + nmax;
+  m.w = reinterpret_cast<u32*>(m.V + (compact ? nmax : 2 * nmax));
   m.wpre = m.w + line_wn(S, k);
   m.scr = m.wpre + line_wn(S, k);
   m.acc = m.scr + 64;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_cmin(Group g, LineCfg lc,
   const u32 K32 = (k - 1 + 31) / 32 * 32;              // span starts K32 cells before x0
   const u32 nbits = K32 + Se + k - 1 + 32;
   const u32 nwords = (nbits + 31) / 32;
-  const LineSmem m = line_smem(smem_raw, lc.nmax, lc.S, k);
+  const LineSmem m = line_smem(smem_raw, lc.nmax, lc.S, k, lc.compact != 0);
   u64 *V = m.V, *Q = m.Q, *wv = m.wv;
   u32 *w = m.w, *wpre = m.wpre, *scr = m.scr, *wf = m.wf;
   const u32* bits = (F == 0 ? occw : occT) + ((size_t)s * L + line) * T;
@@ -235,10 +239,21 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_cmin(Group g, LineCfg lc,
     V[u] = v;
   }
   __syncthreads();
-  block_seg_scan<false>(V, Q, n, k, wv, wf);
-  block_seg_scan<true>(V, V, n, k, wv, wf);
   u64* out = (F == 0 ? cA : cB) + ((size_t)s * L + line) * L;
-  for (u32 v = threadIdx.x; v < Se; v += blockDim.x) out[x0 + v] = tmin(Q[v], V[v + k - 1]);
+  if (lc.compact) {
+    // Se <= S <= k: the span [0, Se + k - 1) holds two k-blocks.  The windows
+    // need suffix minima only inside the first block ([0, k), in place) and
+    // prefix minima only inside the second ([k, n), in place); the prefix
+    // minimum at k - 1 closing the first block is its suffix minimum at 0.
+    block_seg_scan<false>(V, V, k, k, wv, wf);
+    if (n > k) block_seg_scan<true>(V + k, V + k, n - k, k, wv, wf);
+    for (u32 v = threadIdx.x; v < Se; v += blockDim.x)
+      out[x0 + v] = tmin(V[v], v == 0 ? V[0] : V[v + k - 1]);
+  } else {
+    block_seg_scan<false>(V, Q, n, k, wv, wf);
+    block_seg_scan<true>(V, V, n, k, wv, wf);
+    for (u32 v = threadIdx.x; v < Se; v += blockDim.x) out[x0 + v] = tmin(Q[v], V[v + k - 1]);
+  }
   if (__syncthreads_or(any) && threadIdx.x == 0 && !g.st[s].alive) g.st[s].alive = 1;
 }
 

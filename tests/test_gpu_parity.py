@@ -223,3 +223,11 @@ def test_bisection_probes_are_logarithmic_in_n_j(L, k):
     for i in range(16):
         assert st["probes"][i] <= 1 + int(np.ceil(np.log2(int(nj[i])))), (i, st["probes"][i], nj[i])
     lat.close()
+
+
+@pytest.mark.parametrize("L,k", [(4096, 3500), (3328, 3328)])
+def test_windows_longer_than_a_segment(L, k):
+    # windows so long that a segment of the line pass is at most k cells: the
+    # window-minimum pass keeps one value array (two k-blocks per segment);
+    # 4096 / 3500 also has a ragged second segment and k not a multiple of 32
+    _check(L, k, [1], configs=1)
