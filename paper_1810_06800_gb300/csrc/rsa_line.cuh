@@ -294,6 +294,7 @@ constexpr u16 CODE_V = 0x8000;
 
 __global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, const u64* cB,
                                                     u16* code, u16* codeT) {
+  __shared__ u64 tb[32][33];
   __shared__ u16 tc[32][34];
   const u32 s = blockIdx.y;
   if (g.st[s].done) return;
@@ -304,11 +305,17 @@ __global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, cons
   u16* C = code + (size_t)s * g.LL;
   u16* CT = codeT + (size_t)s * g.LL;
   const u64 zb = g.base[s] + SM_GAMMA;
+  // the vertical minima of the tile, read along their own rows (columns x)
+  for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
+    const u32 r = i >> 5, c = i & 31;                 // (x, y) = (tx*32 + r, ty*32 + c)
+    tb[r][c] = B[(size_t)(tx * 32 + r) * L + ty * 32 + c];
+  }
+  __syncthreads();
   for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
     const u32 r = i >> 5, c = i & 31;                 // cell (y, x) = (ty*32 + r, tx*32 + c)
     const u32 y = ty * 32 + r, x = tx * 32 + c;
     const u64 vh = A[(size_t)y * L + x];
-    const u64 vv = B[(size_t)x * L + y];
+    const u64 vv = tb[c][r];
     u16 out = CODE_NONE;
     if (vh != vv) {
       const u64 m = vh < vv ? vh : vv;
@@ -451,17 +458,19 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_accept_codes(Group g, Lin
   const u32 Se = min(lc.S, L - x0);
   const u32 n = Se + k - 1;                  // codes x0 .. x0+n-1
   const u32 nwords = (n + 31) / 32;
-  u16* cv = reinterpret_cast<u16*>(smem_raw);                 // n (+1) codes
-  u32* brk = reinterpret_cast<u32*>(cv + ((lc.nmax + 2 + 1) & ~1u));
+  u16* cv = reinterpret_cast<u16*>(smem_raw);                 // n (+1) codes, 8-code chunks
+  u32* brk = reinterpret_cast<u32*>(cv + ((lc.nmax + 9) & ~7u));
   u32* pre = brk + ((lc.nmax + 31) / 32 + 2);
   u32* scr = pre + ((lc.nmax + 31) / 32 + 2);
   __shared__ u32 nacc, node_sh;
   __shared__ u32 acc[LINE_ACC];
   const u16* row = (F == 0 ? code : codeT) + ((size_t)s * L + line) * L;
-  for (u32 u = threadIdx.x; u <= n; u += blockDim.x) {
+  // codes x0 .. x0+n (around the torus) in 16-byte chunks: x0 and L are
+  // multiples of 32, so a chunk of 8 never crosses the end of the line
+  for (u32 u = threadIdx.x * 8; u <= n; u += blockDim.x * 8) {
     u32 p = x0 + u;
     while (p >= L) p -= L;
-    cv[u] = row[p];
+    *reinterpret_cast<uint4*>(cv + u) = __ldg(reinterpret_cast<const uint4*>(row + p));
   }
   if (threadIdx.x == 0) nacc = 0;
   __syncthreads();
@@ -512,7 +521,7 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_accept_codes(Group g, Lin
 }
 
 __host__ __device__ inline size_t line_codes_smem_bytes(u32 nmax) {
-  return (size_t)((nmax + 2 + 1) & ~1u) * 2 + (size_t)((nmax + 31) / 32 + 2) * 8 + 64 * 4;
+  return (size_t)((nmax + 9) & ~7u) * 2 + (size_t)((nmax + 31) / 32 + 2) * 8 + 64 * 4;
 }
 
 }  // namespace rsak
