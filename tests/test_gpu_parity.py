@@ -83,6 +83,20 @@ def test_scale_config_sampled_seeds():
     _check(w["L"], w["k"], seeds, configs=2)
 
 
+def test_bench_launch_configuration_sampled():
+    # the benchmark's own launch: seeds 1..1000 of L = 1024, k = 32 in one
+    # batch; every 50th sample (and the last) checked against the oracle
+    w = workloads.PLAIN_SCALE
+    seeds = np.asarray(w["seeds"], dtype=np.uint64)
+    assert seeds.size == 1000
+    lat = rsa.Lattice(w["L"], w["k"])
+    nj, nc = lat.run(seeds)
+    pick = list(range(0, 1000, 50)) + [999]
+    wj, wc = _oracle_many(w["L"], w["k"], [int(seeds[i]) for i in pick])
+    assert np.array_equal(nj[pick], wj) and np.array_equal(nc[pick], wc)
+    lat.close()
+
+
 @pytest.mark.parametrize("L,k", [(1024, 512), (2048, 1024), (4100, 2050)])
 def test_long_windows(L, k):
     _check(L, k, [3, 4], configs=1)
