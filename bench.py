@@ -65,6 +65,10 @@ OPS_PER_CELL = {
     # (two byte compares and an add); keys only for accepted candidates
     "k_tile_accept": 2 * 3,
 }
+# long-k path: work counter holding each kernel's processed cells, and the
+# share of it that kernel did (the two acceptance passes share one counter)
+LINE_WORK = {"k_line_cmin_h": (0, 1.0), "k_line_cmin_v": (1, 1.0), "k_line_accept_h": (2, 0.5),
+             "k_line_accept_v": (2, 0.5), "k_line_codes": (3, 1.0)}
 TILE_WORK = {"k_tile_cmin": ("cmin_cells", "cmin_keys"),
              "k_tile_accept": ("accept_cells", "accept_keys")}
 ALU_LANES_PER_SM = 128  # 4 schedulers x 32 lanes, one integer op per lane per clock
@@ -360,11 +364,16 @@ def main():
                              "peak_gbs": hbm_peak,
                              "frac": 1.0 * cells / (dom_ms / 1e3) / 1e9 / hbm_peak}}
     elif dom in BYTES_PER_CELL:
-        alg_bytes = BYTES_PER_CELL[dom] * passes * L * L
+        if dom in LINE_WORK:   # cells of segments / tiles not skipped as dead
+            ctr, share = LINE_WORK[dom]
+            cells = work["raw"][ctr] * share
+        else:
+            cells = passes * L * L
+        alg_bytes = BYTES_PER_CELL[dom] * cells
         achieved = alg_bytes / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": (ent["bytes_per_cell"] * passes * L * L / dom_launches) if fresh else None,
+                "traffic": (ent["bytes_per_cell"] * cells / dom_launches) if fresh else None,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "alg_bytes_per_launch": alg_bytes / dom_launches}
     else:

@@ -149,11 +149,14 @@ int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_
 int rsa_profile(rsa_t *h, int enable);
 int rsa_kernel_stats(rsa_t *h, double *ms, unsigned long long *launches, uint32_t n_kinds);
 const char *rsa_kernel_name(uint32_t kind);
-/* Work done by the tiled round kernels since the previous call (then reset):
- * out[0] cells of live tiles processed by the cell-minimum pass, out[1]
- * live candidates it gave a priority, out[2] / out[3] the same for the
- * acceptance pass (n <= 4 values are written).  Zero for shapes that do not
- * use the tiled kernels. */
+/* Work done by the round kernels since the previous call (then reset; n <= 4
+ * values are written).  Tile path (power-of-two k <= 32): out[0] cells of live
+ * tiles processed by the cell-minimum pass, out[1] live candidates it gave a
+ * priority, out[2] / out[3] cells and accepted candidates of the acceptance
+ * pass.  Long-k path: out[0] / out[1] cells processed by the horizontal /
+ * vertical window-minimum passes, out[2] by the acceptance passes, out[3] by
+ * the code pass (segments and tiles without live candidates are skipped and
+ * not counted).  Zero on the general path. */
 int rsa_work_stats(rsa_t *h, unsigned long long *out, uint32_t n);
 
 /* Bytes of device workspace a run of n_samples needs for (L, k). */

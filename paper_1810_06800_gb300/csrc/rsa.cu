@@ -50,7 +50,7 @@ size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
   size_t occ, occw, occT, cB, code16, code16T, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
-      ebkt, nkey_b, nbkt, st, seeds, counters, keys,
+      ebkt, nkey_b, nbkt, st, seeds, counters, work, keys,
       scratch, total;
 };
 
@@ -177,7 +177,10 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   l.cB = take(G.line ? n * LL * 8 : 0);
   l.code16 = take(G.line ? n * LL * 2 : 0);
   l.code16T = take(G.line ? n * LL * 2 : 0);
-  l.dead = take(G.tile ? (size_t)n * G.tc.T2 : 0);
+  // dead flags: per 32 x 32 tile (tile path); per line segment of each
+  // orientation, then per 32 x 32 code tile (long-k path)
+  l.dead = take(G.tile ? (size_t)n * G.tc.T2
+                       : G.line ? (size_t)n * (2ull * L * G.lc.nseg + G.tc.T2) : 0);
   l.owner = take(n * LL * 4);
   l.cmin = take(n * LL * (G.tile ? 1 : 8));  // tile path: one argmin code byte per cell
   l.base = take((size_t)n * 8);
@@ -193,6 +196,7 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   l.st = take((size_t)n * sizeof(SampleState));
   l.seeds = take((size_t)n * 8);
   l.counters = take(64);
+  l.work = take(4 * WORK_SLOTS * 8);
   l.keys = take(with_keys ? 2 * LL * 8 : 0);
   // scratch blocks are indexed by (sample, block) in the kernels
   l.scratch = take(bits ? 0 : G.scratch_words * 8 * n);
@@ -247,8 +251,8 @@ struct rsa {
   u32 last_n = 0;
   bool with_keys = false;
   cudaStream_t stream = nullptr;
-  u32* h_counter = nullptr;  // pinned, 64 bytes: loop counters + work counters
-  unsigned long long work[4] = {0, 0, 0, 0};  // accumulated tile-pass work
+  u32* h_counter = nullptr;  // pinned, 64 bytes: loop counters, configuration bits
+  unsigned long long work[4] = {0, 0, 0, 0};  // accumulated round-pass work
   int device = -1;
   int sm_count = 0;
   int tile_blocks[2] = {0, 0};  // resident blocks per SM: cmin, accept
@@ -325,7 +329,7 @@ Group group_of(rsa_t* h, u32 n) {
   g.edges = reinterpret_cast<Edge*>(b + l.edges);
   g.st = reinterpret_cast<SampleState*>(b + l.st);
   g.scratch = reinterpret_cast<u64*>(b + l.scratch);
-  g.work = reinterpret_cast<u64*>(b + l.counters + 16);
+  g.work = reinterpret_cast<u64*>(b + l.work);
   return g;
 }
 
@@ -495,11 +499,14 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   } else if (G.line) {
     CUDA_TRY(cudaMemsetAsync(b + l.occw, 0, (size_t)n * LL / 8, stream));
     CUDA_TRY(cudaMemsetAsync(b + l.occT, 0, (size_t)n * LL / 8, stream));
+    CUDA_TRY(cudaMemsetAsync(b + l.dead, 0, (size_t)n * (2ull * h->L * G.lc.nseg + G.tc.T2),
+                             stream));
   } else {
     CUDA_TRY(cudaMemsetAsync(g.occ, 0, (size_t)n * LL, stream));
   }
   CUDA_TRY(cudaMemsetAsync(g.owner, 0xFF, (size_t)n * LL * 4, stream));
   CUDA_TRY(cudaMemsetAsync(b + l.counters, 0, 64, stream));
+  CUDA_TRY(cudaMemsetAsync(b + l.work, 0, 4 * WORK_SLOTS * 8, stream));
   launch(h, KD_INIT, k_init, dim3((n + 127) / 128), dim3(128), 0, stream, g,
          (const u64*)d_seeds);
   if ((rc = launch_check("k_init"))) return rc;
@@ -543,10 +550,12 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
         if (launch_tile(h, g, tc, occw, dead, tgrid, st)) body_rc = RSA_EINVAL;
       } else if (G.line) {
         const dim3 lg(h->L * G.lc.nseg, n), tg(G.tc.T2, n);
+        u8* ldead = dead;                                          // [n][2][L][nseg]
+        u8* cdead = dead + (size_t)n * 2 * h->L * G.lc.nseg;       // [n][T^2]
         launch(h, KD_LINE_CMIN_H, k_line_cmin<0>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
-               G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
+               G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB, ldead);
         launch(h, KD_LINE_CMIN_V, k_line_cmin<1>, lg, dim3(LINE_THREADS), G.line_smem, st, g,
-               G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB);
+               G.lc, (const u32*)occw, (const u32*)occT, g.cmin, cB, ldead);
         if (h->with_keys) {
           // caller-supplied priorities cannot be inverted: compare values
           launch(h, KD_LINE_COMBINE, k_line_combine, tg, dim3(256), 0, st, g, g.cmin, cB);
@@ -558,11 +567,13 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
           u16* c16 = reinterpret_cast<u16*>(b + l.code16);
           u16* c16T = reinterpret_cast<u16*>(b + l.code16T);
           launch(h, KD_LINE_CODES, k_line_codes, tg, dim3(256), 0, st, g, (const u64*)g.cmin,
-                 (const u64*)cB, c16, c16T);
+                 (const u64*)cB, c16, c16T, cdead);
           launch(h, KD_LINE_ACCEPT_H, k_line_accept_codes<0>, lg, dim3(LINE_THREADS),
-                 G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T);
+                 G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T,
+                 (const u8*)ldead);
           launch(h, KD_LINE_ACCEPT_V, k_line_accept_codes<1>, lg, dim3(LINE_THREADS),
-                 G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T);
+                 G.line_codes_smem, st, g, G.lc, occw, occT, (const u16*)c16, (const u16*)c16T,
+                 (const u8*)ldead);
         }
       } else {
         launch(h, KD_ROW_CMIN, k_row<0>, rg, dim3(G.row_threads), G.row_smem, st, g, G.row);
@@ -626,12 +637,11 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
       break;
     }
   }
-  // tile-pass work counters of this run (for throughput accounting)
-  CUDA_TRY(cudaMemcpyAsync(h->h_counter + 4, b + l.counters + 16, 32, cudaMemcpyDeviceToHost,
-                           stream));
+  // round-pass work counters of this run (for throughput accounting)
+  unsigned long long wk[4 * WORK_SLOTS];
+  CUDA_TRY(cudaMemcpyAsync(wk, b + l.work, sizeof(wk), cudaMemcpyDeviceToHost, stream));
   CUDA_TRY(cudaStreamSynchronize(stream));
-  const unsigned long long* wk = reinterpret_cast<const unsigned long long*>(h->h_counter + 4);
-  for (int i = 0; i < 4; ++i) h->work[i] += wk[i];
+  for (u32 i = 0; i < 4 * WORK_SLOTS; ++i) h->work[i / WORK_SLOTS] += wk[i];
   return 0;
 }
 

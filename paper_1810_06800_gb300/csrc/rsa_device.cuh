@@ -34,6 +34,9 @@ constexpr u64 SM_GAMMA = 0x9E3779B97F4A7C15ull;  // splitmix64 increment
 constexpr u32 NONE32 = 0xFFFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr u32 OWN_V = 1u << 31;  // owner word: set for a vertical k-mer's cells
+// Work counters are spread over WORK_SLOTS addresses (by block index), so that
+// many blocks adding to one counter do not queue on a single L2 address.
+constexpr u32 WORK_SLOTS = 32;
 constexpr u32 NBKT = 256;  // time buckets (top 8 bits of a priority)
 
 // status bits (per sample), mapped to RSA_E* codes by the host
@@ -105,9 +108,16 @@ struct Group {         // one batch of samples sharing (L, k)
   u32* nbkt;           // [n][NBKT + 1] bucket offsets into nkey_b
   SampleState* st;     // [n]
   u64* scratch;        // global scratch for very long windows (or null)
-  u64* work;           // [4] work counters of the tile passes: cmin cells,
-                       //     cmin keys, accept cells, accept keys
+  u64* work;           // [4][WORK_SLOTS] work counters of the round passes (tile path:
+                       //     cmin cells, cmin keys, accept cells, accept keys; long-k
+                       //     path: horizontal and vertical window-minimum cells,
+                       //     acceptance cells, code cells)
 };
+
+// Add v to work counter c (slot chosen by the block index).
+__device__ __forceinline__ void work_add(const Group& g, u32 c, u64 v) {
+  atomicAdd(g.work + c * WORK_SLOTS + (blockIdx.x & (WORK_SLOTS - 1)), v);
+}
 
 __device__ __forceinline__ u64 cand_key(const Group& g, u32 s, u64 idx) {
   if (g.keys) return g.keys[idx];

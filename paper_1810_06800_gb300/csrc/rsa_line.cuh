@@ -200,16 +200,23 @@ __device__ inline LineSmem line_smem(unsigned char* raw, u32 nmax, u32 S, u32 k,
 // Per-cell minimum of live priorities of one orientation along lines.
 // F = 0: lines are rows y of occw, output cA[y][.]; F = 1: lines are columns
 // x (rows of the transposed bits occT), output cB[x][.].
+// ldead[((s * 2 + F) * L + line) * nseg + seg] is set once a segment's span
+// holds no live candidate: its outputs were written as "none" in that round
+// and stay so (candidates only die), so later rounds skip it.
 template <int F>
 __global__ void __launch_bounds__(LINE_THREADS) k_line_cmin(Group g, LineCfg lc, const u32* occw,
-                                                            const u32* occT, u64* cA, u64* cB) {
+                                                            const u32* occT, u64* cA, u64* cB,
+                                                            u8* ldead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const u32 s = blockIdx.y;
   if (g.st[s].done) return;
   const u32 L = g.L, k = g.k, T = lc.T;
   const u32 line = blockIdx.x / lc.nseg, seg = blockIdx.x % lc.nseg;
+  u8* dflag = ldead + ((size_t)(s * 2 + F) * L + line) * lc.nseg + seg;
+  if (*dflag) return;
   const u32 x0 = seg * lc.S;
   const u32 Se = min(lc.S, L - x0);
+  if (threadIdx.x == 0) work_add(g, F, Se);
   const u32 n = Se + k - 1;
   const u32 K32 = (k - 1 + 31) / 32 * 32;              // span starts K32 cells before x0
   const u32 nbits = K32 + Se + k - 1 + 32;
@@ -254,7 +261,11 @@ __global__ void __launch_bounds__(LINE_THREADS) k_line_cmin(Group g, LineCfg lc,
     block_seg_scan<true>(V, V, n, k, wv, wf);
     for (u32 v = threadIdx.x; v < Se; v += blockDim.x) out[x0 + v] = tmin(Q[v], V[v + k - 1]);
   }
-  if (__syncthreads_or(any) && threadIdx.x == 0 && !g.st[s].alive) g.st[s].alive = 1;
+  if (__syncthreads_or(any)) {
+    if (threadIdx.x == 0 && !g.st[s].alive) g.st[s].alive = 1;
+  } else if (threadIdx.x == 0) {
+    *dflag = 1;
+  }
 }
 
 // cmin = min(cA[y][x], cB[x][y]) into both layouts, one 32 x 32 tile of each.
@@ -292,19 +303,25 @@ __global__ void __launch_bounds__(256) k_line_combine(Group g, u64* cA, u64* cB)
 constexpr u16 CODE_NONE = 0xFFFF;
 constexpr u16 CODE_V = 0x8000;
 
+// cdead[s * T^2 + tile] is set once every code of the 32 x 32 tile is
+// CODE_NONE; they stay so, and later rounds skip the tile.
 __global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, const u64* cB,
-                                                    u16* code, u16* codeT) {
+                                                    u16* code, u16* codeT, u8* cdead) {
   __shared__ u64 tb[32][33];
   __shared__ u16 tc[32][34];
   const u32 s = blockIdx.y;
   if (g.st[s].done) return;
   const u32 L = g.L, T = L / 32;
+  u8* dflag = cdead + (size_t)s * T * T + blockIdx.x;
+  if (*dflag) return;
+  if (threadIdx.x == 0) work_add(g, 3, 1024);
   const u32 ty = blockIdx.x / T, tx = blockIdx.x % T;
   const u64* A = cA + (size_t)s * g.LL;
   const u64* B = cB + (size_t)s * g.LL;
   u16* C = code + (size_t)s * g.LL;
   u16* CT = codeT + (size_t)s * g.LL;
   const u64 zb = g.base[s] + SM_GAMMA;
+  bool any = false;
   // the vertical minima of the tile, read along their own rows (columns x)
   for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
     const u32 r = i >> 5, c = i & 31;                 // (x, y) = (tx*32 + r, ty*32 + c)
@@ -334,8 +351,9 @@ __global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, cons
     }
     C[(size_t)y * L + x] = out;
     tc[r][c] = out;
+    any |= out != CODE_NONE;
   }
-  __syncthreads();
+  if (!__syncthreads_or(any) && threadIdx.x == 0) *dflag = 1;
   for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
     const u32 r = i >> 5, c = i & 31;                 // row x = tx*32 + r of the transpose
     CT[(size_t)(tx * 32 + r) * L + ty * 32 + c] = tc[c][r];
@@ -448,14 +466,19 @@ template <int F>
 __global__ void __launch_bounds__(LINE_THREADS) k_line_accept_codes(Group g, LineCfg lc,
                                                                     u32* occw, u32* occT,
                                                                     const u16* code,
-                                                                    const u16* codeT) {
+                                                                    const u16* codeT,
+                                                                    const u8* ldead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const u32 s = blockIdx.y;
   if (g.st[s].done) return;
   const u32 L = g.L, k = g.k, T = lc.T;
   const u32 line = blockIdx.x / lc.nseg, seg = blockIdx.x % lc.nseg;
+  // no live candidate anchored in this segment (its window-minimum span,
+  // which contains these anchors, had none this round)
+  if (ldead[((size_t)(s * 2 + F) * L + line) * lc.nseg + seg]) return;
   const u32 x0 = seg * lc.S;
   const u32 Se = min(lc.S, L - x0);
+  if (threadIdx.x == 0) work_add(g, 2, Se);
   const u32 n = Se + k - 1;                  // codes x0 .. x0+n-1
   const u32 nwords = (n + 31) / 32;
   u16* cv = reinterpret_cast<u16*>(smem_raw);                 // n (+1) codes, 8-code chunks

@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
   const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 dirw = warp >> 1, half = warp & 1;
   const u32 L = g.L, T = tc.T, T2 = tc.T2;
+  u32 cells_sum = 0, keyed_sum = 0;  // work of this block, added once at the end
   for (ItemIter it(blockIdx.x, T2); it.s < g.n; it.next(gridDim.x, T2)) {
     const u32 s = it.s, t = it.t;
     if (g.st[s].done) continue;
@@ -327,8 +328,7 @@ __global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
     if (lane == 0 && live) atomicOr(&live_sh[dirw], live);
     __syncthreads();
     const u32 lhb = live_sh[0], lvb = live_sh[1];
-    keyed = __reduce_add_sync(FULL, keyed);
-    if (lane == 0 && keyed) atomicAdd(g.work + 1, (u64)keyed);
+    keyed_sum += __reduce_add_sync(FULL, keyed);
     if ((lhb | lvb) == 0) {
       // no live candidate on or before any line: every cell is uncovered
       if (threadIdx.x == 0) *dflag = 1;
@@ -428,11 +428,13 @@ __global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
     }
     const bool tile_live = __syncthreads_or(any);
     if (threadIdx.x == 0) {
-      atomicAdd(g.work + 0, 1024ull);
+      cells_sum += 1024;
       if (!tile_live) *dflag = 1;
       else if (!g.st[s].alive) g.st[s].alive = 1;
     }
   }
+  if (threadIdx.x == 0 && cells_sum) work_add(g, 0, cells_sum);
+  if (lane == 0 && keyed_sum) work_add(g, 1, keyed_sum);
 }
 
 // Pass 2 of a round: acceptance of candidates anchored in each live tile.
@@ -450,13 +452,14 @@ __global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
 //      cells is OR-ed into the occupancy words once per line, and the owner
 //      ids of each accepted k-mer's cells are one warp-wide store.
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg tc, u32* occw,
+__global__ void __launch_bounds__(TILE_THREADS, 12) k_tile_accept(Group g, TileCfg tc, u32* occw,
                                                               const u8* dead) {
   __shared__ __align__(16) u8 hc[32][80];   // row y: codes of columns X .. X+63 (+ slack)
   __shared__ __align__(16) u8 vc[65][36];   // row j: codes of rows Y .. Y+63, columns X .. X+31
   const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 dirw = warp >> 1, half = warp & 1;
   const u32 L = g.L, T = tc.T, T2 = tc.T2;
+  u32 cells_sum = 0, accepted_sum = 0;  // work of this block, added once at the end
   for (ItemIter it(blockIdx.x, T2); it.s < g.n; it.next(gridDim.x, T2)) {
     const u32 s = it.s, t = it.t;
     if (g.st[s].done) continue;
@@ -566,10 +569,12 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile_accept(Group g, TileCfg t
       }
       accepted += __popc(m);
     }
-    if (lane == 0 && accepted) atomicAdd(g.work + 3, (u64)accepted);
-    if (threadIdx.x == 0) atomicAdd(g.work + 2, 1024ull);
+    accepted_sum += accepted;
+    cells_sum += 1024;
     __syncthreads();
   }
+  if (threadIdx.x == 0 && cells_sum) work_add(g, 2, cells_sum);
+  if (lane == 0 && accepted_sum) work_add(g, 3, accepted_sum);
 }
 
 }  // namespace rsak

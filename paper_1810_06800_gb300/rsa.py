@@ -215,11 +215,13 @@ def rsa_kernel_stats(h):
 
 
 def rsa_work_stats(h):
-    """Tile-pass work since the previous call: dict of cell and key counts."""
+    """Round-pass work since the previous call: the four counters under their
+    tile-path names, and as ``raw`` (their long-k path meaning differs; see
+    include/rsa.h)."""
     out = np.zeros(4, dtype=np.uint64)
     _check(load().rsa_work_stats(h, out.ctypes.data, 4))
     return dict(cmin_cells=int(out[0]), cmin_keys=int(out[1]), accept_cells=int(out[2]),
-                accept_keys=int(out[3]))
+                accept_keys=int(out[3]), raw=[int(v) for v in out])
 
 
 def rsa_destroy(h):
