@@ -321,6 +321,12 @@ __global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, cons
   u16* C = code + (size_t)s * g.LL;
   u16* CT = codeT + (size_t)s * g.LL;
   const u64 zb = g.base[s] + SM_GAMMA;
+  // exact division by L = 2^lsh * q (q odd): shift, then multiply by the
+  // inverse of q modulo 2^32 (Newton's iteration doubles the correct bits)
+  const u32 lsh = __ffs(L) - 1, q = L >> lsh;
+  u32 lqinv = q;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) lqinv *= 2u - q * lqinv;
   bool any = false;
   // the vertical minima of the tile, read along their own rows (columns x)
   for (u32 i = threadIdx.x; i < 1024; i += blockDim.x) {
@@ -338,14 +344,16 @@ __global__ void __launch_bounds__(256) k_line_codes(Group g, const u64* cA, cons
       const u64 m = vh < vv ? vh : vv;
       const u32 idx = (u32)((mix64_inverse(m) - zb) * SM_GAMMA_INV);
       if (vh < vv) {
-        const u32 xa = (idx / L) * L;            // row start of the anchor
-        u32 d = x + L - (idx - xa);
+        // a horizontal candidate covering (y, x) is anchored on row y
+        u32 d = x + L - (idx - y * L);
         if (d >= L) d -= L;
         out = (u16)d;
       } else {
-        const u32 ya = (idx - (u32)g.LL) / L;
-        u32 d = y + L - ya;
-        if (d >= L) d -= L;
+        // anchored on column x: idx = L^2 + ya L + x, and (y - ya) mod L is
+        // the exact quotient of (y L - ya L) mod L^2 by L
+        u32 dl = y * L - (idx - (u32)g.LL - x);
+        if ((int)dl < 0) dl += (u32)g.LL;
+        const u32 d = (dl >> lsh) * lqinv;
         out = (u16)(CODE_V | d);
       }
     }
