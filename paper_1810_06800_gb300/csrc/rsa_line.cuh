@@ -8,13 +8,17 @@
 //                    priorities along row y            (per-cell minimum, H)
 //   k_line_cmin<1>   cB[x][.] = the same along column x (per-cell minimum, V,
 //                    stored transposed)
-//   k_line_combine   cmin = min(cA[y][x], cB[x][y]) written to both cA[y][x]
-//                    and cB[x][y] (32 x 32 tile transposes through smem)
-//   k_line_accept<F> forward window minima of cA rows (F = 0) / cB rows (F = 1)
-//                    against each live candidate's key.
+//   k_line_codes     per cell, the smaller of the two minima inverted back to
+//                    its candidate (splitmix64 is a bijection): a 2-byte argmin
+//                    code in both layouts (32 x 32 tiles through smem)
+//   k_line_accept_codes<F>  a live candidate is accepted iff its k cells
+//                    carry its codes (start code, then +1 at every step)
+// Caller-supplied priorities have no inverse: for them k_line_combine writes
+// min(cA, cB) to both layouts and k_line_accept<F> compares values.
 // The window minima are van Herk / Gil-Werman over blocks of k cells aligned
 // on the staged span, with block-wide segmented prefix / suffix scans, so the
-// cost per cell does not depend on k.
+// cost per cell does not depend on k.  Segments and code tiles left without
+// live candidates are flagged and skipped in later rounds.
 #pragma once
 #include "rsa_device.cuh"
 

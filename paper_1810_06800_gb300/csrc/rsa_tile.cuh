@@ -5,22 +5,23 @@
 // (row-major, 32 cells per word), so a tile row is exactly one word and a
 // window of k <= 32 cells lies in two adjacent words.  One round is two
 // passes over the tiles:
-//   k_tile_cmin    cmin(cell) = min over live candidates covering the cell,
-//                  horizontal part along the tile's rows, vertical part along
-//                  its columns, both as width-k window minima of the live
+//   k_tile_cmin    per cell, which live candidate covering it has the
+//                  smallest priority, as a 1-byte argmin code: the
+//                  horizontal part along the tile's rows, the vertical part
+//                  along its columns, both width-k window minima of the live
 //                  priorities anchored in the tile and the tile before it;
-//   k_tile_accept  a live candidate anchored in the tile is accepted iff the
-//                  width-k window minimum of cmin over its cells (reaching
-//                  into the tiles right of and below it) equals its key.
-// Each thread owns one line of a tile (a row for horizontal candidates, a
-// column for vertical ones) and computes its width-k window minima
-// sequentially in registers with van Herk / Gil-Werman blocks of k cells
-// (k divides 32, so blocks align with tiles): suffix minima Q of one block,
-// a running prefix minimum P of the next, window = min(Q[i+1], P).  That is
-// O(1) 64-bit minima per cell and no shuffles.
-// A tile whose cmin is all "none" has no live candidate on any of its cells;
-// since live candidates only disappear it stays so, is flagged dead and is
-// skipped by every later pass.
+//   k_tile_accept  a live candidate anchored in the tile is accepted iff it
+//                  is the argmin on every one of its cells (reaching into the
+//                  tiles right of and below it), read from the codes alone.
+// Window minima are van Herk / Gil-Werman with blocks of k cells (k divides
+// 32, so blocks align with tiles): suffix minima Q of the block before, a
+// running prefix minimum P of the next, window = min(Q[i+1], P); O(1) 64-bit
+// minima per cell and no shuffles.  For k < 32 one thread walks each live
+// line in registers; for k = 32 one thread builds Q and another P of each
+// live line in shared memory, and the write-out combines them.
+// A tile whose codes are all "none" has no live candidate on any of its
+// cells; since live candidates only disappear it stays so, is flagged dead
+// and is skipped by every later pass.
 #pragma once
 #include "rsa_device.cuh"
 
