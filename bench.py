@@ -392,8 +392,13 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
         rate, m, secs = cpu_oracle_rate(L, k, [int(s) for s in seeds], args.cpu_seconds, cores)
+        # the same oracle on one core, over a shorter prefix of the seeds
+        rate1, m1, secs1 = cpu_oracle_rate(L, k, [int(s) for s in seeds],
+                                           max(1.0, args.cpu_seconds / 5), 1)
         cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {m} seeds of {args.workload} ({secs:.1f} s on {cores} threads)"}
+               "sample": f"first {m} seeds of {args.workload} ({secs:.1f} s on {cores} threads)",
+               "single_core": {"value": rate1, "unit": "samples/s",
+                               "sample": f"first {m1} seeds ({secs1:.1f} s on 1 thread)"}}
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
