@@ -447,13 +447,16 @@ __global__ void __launch_bounds__(TILE_THREADS, K >= 16 ? 6 : 5)
 // INC(x .. x+K-2).  No priority is needed except for the accepted ones.
 //  (a) stage the codes of the tile, the tile to the right (rows) and the
 //      tile below (columns); a dead neighbour reads as ARG_NONE;
+//  Sixteen 128-thread blocks per SM (32 registers): the pass is latency-bound
+//  on its staging and ballots, and full occupancy hides that best (measured
+//  3.7% faster for the whole L=1024, k=32 run than twelve blocks at 40).
 //  (b) warps 0-1 take 16 rows each, warps 2-3 16 columns each; the accepted
 //      candidates of a line (disjoint k-mers) get consecutive nodes from one
 //      atomic, each accepting lane records its own node, the union of their
 //      cells is OR-ed into the occupancy words once per line, and the owner
 //      ids of each accepted k-mer's cells are one warp-wide store.
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS, 12) k_tile_accept(Group g, TileCfg tc, u32* occw,
+__global__ void __launch_bounds__(TILE_THREADS, 16) k_tile_accept(Group g, TileCfg tc, u32* occw,
                                                               const u8* dead) {
   __shared__ __align__(16) u8 hc[32][80];   // row y: codes of columns X .. X+63 (+ slack)
   __shared__ __align__(16) u8 vc[65][36];   // row j: codes of rows Y .. Y+63, columns X .. X+31
