@@ -504,7 +504,9 @@ __global__ void k_probe_copy(Group g) {
     Wd[m] = S[m];
 }
 
-__global__ void k_probe(Group g) {
+// Eight 256-thread blocks per SM (32 registers): probes are latency-bound
+// union-find walks, and full occupancy hides more of that latency.
+__global__ void __launch_bounds__(256, 8) k_probe(Group g) {
   const u32 s = blockIdx.y;
   SampleState& st = g.st[s];
   if (st.sdone) return;
