@@ -1,16 +1,21 @@
 #!/usr/bin/env python3
 """Throughput benchmark: jammed RSA samples per second on one GB300.
 
-Workload (default): L = 1024 periodic lattice, k = 32, 1000 samples with
-seeds 1..1000 per step (per rank under torchrun; rank r uses seeds
-r*1000 + 1 ..).  One step runs the whole path for the batch: the parallel
-greedy rounds to jamming (n_j), the contact graph, and the first-wrap
-bisection (n_c).  Prints one JSON line.
+Workload (default): the large-k batch, L = 32768 periodic lattice, k = 4096,
+8 samples with seeds 1..8 per step (per rank under torchrun; rank r uses
+seeds r*8 + 1 ..), 209 GB held on the device.  One step runs the whole path
+for the batch: the parallel greedy rounds to jamming (n_j), the contact
+graph, and the first-wrap bisection (n_c).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
 
-`--impl reference` times the CPU oracle (a plain sequential scan plus
-union-find in C) on the host cores, on a bounded sample of the same workload.
+`value` is timed on the product path (graph-replayed round and probe loops,
+no per-kernel events).  A separate profiled pass of the same steps records a
+CUDA event pair around every launch for the per-kernel shares and the
+roofline of the dominant kernel.  `--impl reference` times the CPU oracle (a
+plain sequential scan plus union-find in C) on the host cores, on a bounded
+sample of the same workload.
 """
 from __future__ import annotations
 
@@ -29,50 +34,67 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    # the largest single-GPU configuration: the default
+    "L32768_k4096_x8": dict(L=32768, k=4096, n=8),
     "L1024_k32_x1000": dict(L=1024, k=32, n=1000),
     "L64_k4_x100": dict(L=64, k=4, n=100),
     # small cases for ncu captures (a few GB on the device)
     "L1024_k32_x64": dict(L=1024, k=32, n=64),
     "L8192_k512_x2": dict(L=8192, k=512, n=2),
-    # large k held on the device: 8 samples of L = 32768 (1 G cells each)
-    "L32768_k4096_x8": dict(L=32768, k=4096, n=8),
+    "L8192_k512_x8": dict(L=8192, k=512, n=8),
 }
+DEFAULT_WORKLOAD = "L32768_k4096_x8"
 METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
-# Algorithmic work of the round kernels.  Byte-type kernels (the general
-# line path): bytes per lattice cell per launch -- the cell-minimum passes
-# read occupancy (1 B) and write or read-modify-write the 8-byte cell
-# minimum, the acceptance passes read it.
-BYTES_PER_CELL = {"k_row_cmin": 9, "k_col_cmin": 17, "k_row_accept": 8, "k_col_accept": 8,
-                  # long-k line path: window minima write the 8-byte minimum of
-                  # one orientation and read occupancy bits; the combine reads
-                  # both minima and writes two 2-byte argmin codes; acceptance
-                  # reads one code per cell and occupancy bits
-                  "k_line_cmin_h": 8.125, "k_line_cmin_v": 8.125, "k_line_codes": 20,
-                  "k_line_accept_h": 2.125, "k_line_accept_v": 2.125}
-# Integer-ALU kernels (the 32x32 tile path), counted in 32-bit lane
-# operations: a 64-bit minimum is 4 ops (two compares, two selects) plus 1
-# when the argmin is tracked, a width-k window minimum by van Herk /
-# Gil-Werman is 3 minima per cell, a liveness test of a candidate's k cells
-# is 4 ops (shift, mask, compare of a 64-bit word), a splitmix64 priority is
-# 20 ops (64-bit add 2, three 64-bit xor-shifts at 4, two 64-bit constant
-# multiplies at 3).
-OPS_PER_KEY = 20
-OPS_PER_CELL = {
-    # horizontal and vertical argmin window minima, their combination into a
-    # one-byte code (min + select), two liveness tests
-    "k_tile_cmin": 2 * 3 * 5 + 6 + 2 * 4,
-    # per direction: "code is the start value" and "next code is this + 1"
-    # (two byte compares and an add); keys only for accepted candidates
-    "k_tile_accept": 2 * 3,
-}
-# long-k path: work counter holding each kernel's processed cells, and the
-# share of it that kernel did (the two acceptance passes share one counter)
-LINE_WORK = {"k_line_cmin_h": (0, 1.0), "k_line_cmin_v": (1, 1.0), "k_line_accept_h": (2, 0.5),
-             "k_line_accept_v": (2, 0.5), "k_line_codes": (3, 1.0)}
-TILE_WORK = {"k_tile_cmin": ("cmin_cells", "cmin_keys"),
-             "k_tile_accept": ("accept_cells", "accept_keys")}
-ALU_LANES_PER_SM = 128  # 4 schedulers x 32 lanes, one integer op per lane per clock
 
+# Algorithmic bytes per processed lattice cell of each round kernel, from
+# the byte model of the method's unfused steps: rowmin reads a priority and
+# writes a cell minimum (8 + 8); colmin reads a priority and the row minimum
+# and writes their minimum (8 + 8 + 8); accept reads the cell minimum along
+# both orientations and both priorities (2 x 8 + 16); kill reads occupancy
+# (1).  A kernel that carries out several of these steps is credited with
+# their sum over the cells it processed; where two kernels split one step,
+# each is credited with the part it does.  Priorities are recomputed rather
+# than stored and minima are kept as short argmin codes, so the kernels move
+# far fewer DRAM bytes than this (ncu "traffic").
+STEP_BYTES = {"rowmin": 16.0, "colmin": 24.0, "accept": 32.0, "kill": 1.0}
+KERNEL_STEPS = {
+    # 32 x 32 tile path: one pass both window minima, one pass acceptance
+    "k_tile_cmin": (("rowmin", "colmin"), 40.0),
+    "k_tile_accept": (("accept", "kill"), 33.0),
+    # long-k line path: horizontal windows (rowmin); vertical windows (the
+    # window part of colmin, 16 of its 24 bytes); the per-cell combine of
+    # the two minima (the remaining 8); acceptance along rows / columns (half
+    # of accept + kill each)
+    "k_line_cmin_h": (("rowmin",), 16.0),
+    "k_line_cmin_v": (("colmin",), 16.0),
+    "k_line_codes": (("colmin",), 8.0),
+    "k_line_combine": (("colmin",), 8.0),
+    "k_line_accept_h": (("accept", "kill"), 16.5),
+    "k_line_accept_v": (("accept", "kill"), 16.5),
+    # general path
+    "k_row_cmin": (("rowmin",), 16.0),
+    "k_col_cmin": (("colmin",), 24.0),
+    "k_row_accept": (("accept", "kill"), 16.5),
+    "k_col_accept": (("accept", "kill"), 16.5),
+}
+# Processed cells per kernel: (work counter, share of it).  Tile path
+# counters: 0 cmin cells, 1 cmin keys, 2 accept cells, 3 accept keys; long-k
+# path: 0 / 1 horizontal / vertical window cells, 2 acceptance cells (both
+# orientations), 3 combine cells.  The general path has no counters: every
+# cell of every round.
+WORK_CELLS = {"k_tile_cmin": (0, 1.0), "k_tile_accept": (2, 1.0),
+              "k_line_cmin_h": (0, 1.0), "k_line_cmin_v": (1, 1.0),
+              "k_line_codes": (3, 1.0), "k_line_combine": (3, 1.0),
+              "k_line_accept_h": (2, 0.5), "k_line_accept_v": (2, 0.5)}
+# A second view of the tile kernels, which are bound by integer issue:
+# algorithmic 32-bit lane operations (a 64-bit minimum is 4 ops plus 1 when
+# the argmin is tracked, a window minimum is 3 minima per cell, a liveness
+# test 4 ops, a splitmix64 priority 20 ops) against 128 integer lanes per SM
+# per clock.
+OPS_PER_KEY = 20
+OPS_PER_CELL = {"k_tile_cmin": 2 * 3 * 5 + 6 + 2 * 4, "k_tile_accept": 2 * 3}
+TILE_KEYS = {"k_tile_cmin": 1, "k_tile_accept": 3}
+ALU_LANES_PER_SM = 128
 
 # The source file that holds each kernel: a DRAM-traffic figure measured by
 # ncu is used only while that file is unchanged.
@@ -185,23 +207,50 @@ def max_over_ranks(value: float, pg, device=None) -> float:
     return float(t.item())
 
 
+def oracle_case(L: int, k: int):
+    """(L', k', scale) on which the CPU oracle is timed for workload (L, k).
+    One oracle sample of L >= 4096 takes minutes (about half an hour at
+    L = 32768: a sort of 2 L^2 priorities and a scan), far beyond a bounded
+    baseline, so the oracle then runs the same model at L' = L / 2^j <= 2048
+    with the same L/k, and its rate is scaled to samples of the workload by
+    the lattice sites, scale = (L / L')^2.  The sort costs O(log L) more per
+    site at L than at L', so the scaled rate overstates the oracle's speed
+    at the workload's own size (by about 1.3x at L = 32768)."""
+    j = 0
+    while (L >> j) > 2048 and L % (2 << j) == 0 and k % (2 << j) == 0:
+        j += 1
+    return L >> j, k >> j, float(1 << (2 * j))
+
+
 def cpu_oracle_rate(L, k, seeds, budget_s, threads):
     """Samples/s of the oracle on `threads` host threads over a bounded
-    prefix of the seeds (grown until it takes at least budget_s)."""
+    prefix of the seeds (grown until it takes at least budget_s), on the
+    (possibly scaled-down) case of oracle_case."""
     import oracle
+    Lo, ko, scale = oracle_case(L, k)
     done, t_total, m = 0, 0.0, max(1, threads)
     while True:
         chunk = seeds[done:done + m]
         if not chunk:
             break
         t0 = time.perf_counter()
-        oracle.samples(L, k, chunk, threads=threads)
+        oracle.samples(Lo, ko, chunk, threads=threads)
         t_total += time.perf_counter() - t0
         done += len(chunk)
         if t_total >= budget_s:
             break
         m = min(2 * m, len(seeds) - done) or m
-    return done / t_total, done, t_total
+    return done / t_total / scale, done, t_total, (Lo, ko, scale)
+
+
+def sample_text(wl_name, L, k, m, secs, threads):
+    Lo, ko, scale = oracle_case(L, k)
+    if scale == 1.0:
+        return f"first {m} seeds of {wl_name} ({secs:.1f} s on {threads} threads)"
+    return (f"{m} seeded samples of L={Lo}, k={ko} (the same L/k) in {secs:.1f} s on "
+            f"{threads} threads, scaled by the sites ratio ({L}/{Lo})^2 = {scale:.0f} to "
+            f"samples of L={L}, k={k}; one oracle sample of the workload itself takes "
+            f"minutes")
 
 
 def run_reference(args, wl, world, rank):
@@ -210,24 +259,28 @@ def run_reference(args, wl, world, rank):
     import oracle
     oracle.build()
     L, k, n = wl["L"], wl["k"], wl["n"]
+    Lo, ko, scale = oracle_case(L, k)
     cores = os.cpu_count() or 1
-    seeds = list(range(1, n + 1))
-    per_step = min(n, 2 * cores)
+    seeds = list(range(1, max(n, 2 * cores) + 1))
+    # samples per step: one per core on a scaled-down case, else a bounded
+    # prefix of the workload's own seeds
+    per_step = cores if scale > 1.0 else min(n, 2 * cores)
     for w in range(args.warmup):
-        oracle.samples(L, k, seeds[:per_step], threads=cores)
+        oracle.samples(Lo, ko, seeds[:per_step], threads=cores)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        lo = (s * per_step) % n
-        oracle.samples(L, k, (seeds + seeds)[lo:lo + per_step], threads=cores)
+        lo = (s * per_step) % len(seeds)
+        oracle.samples(Lo, ko, (seeds + seeds)[lo:lo + per_step], threads=cores)
     dt = time.perf_counter() - t0
-    rate = per_step * args.steps / dt
-    sample = f"{per_step} seeds of {args.workload} per step on {cores} threads"
+    rate = per_step * args.steps / dt / scale
+    sample = sample_text(args.workload, L, k, per_step, dt / args.steps, cores) + " (per step)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": args.workload, "L": L, "k": k, "samples_per_step": per_step},
+        "config": {"workload": args.workload, "L": L, "k": k, "samples_per_step": per_step,
+                   "oracle_case": {"L": Lo, "k": ko, "sites_scale": scale}},
         "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0,
@@ -236,13 +289,60 @@ def run_reference(args, wl, world, rank):
     return 0
 
 
+def roofline(dom, kstats, work, passes, L, n_cells_round, hbm_peak, peak_kind, sm_count, sm_mhz):
+    """Roofline of kernel `dom` over the profiled pass: algorithmic bytes per
+    processed cell (KERNEL_STEPS) times the cells its launches processed,
+    over its summed CUDA-event time, against the measured copy bandwidth."""
+    dom_ms, dom_launches = kstats[dom]
+    if dom in WORK_CELLS:
+        ctr, share = WORK_CELLS[dom]
+        cells = work["raw"][ctr] * share
+    else:
+        cells = passes * n_cells_round
+    steps, bpc = KERNEL_STEPS.get(dom, ((), None))
+    out = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "peak": hbm_peak,
+           "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+    if bpc is None or dom_ms <= 0:
+        out.update(achieved=None, frac=None, traffic=None, note="no byte model for this kernel")
+        return out
+    alg = bpc * cells
+    achieved = alg / (dom_ms / 1e3) / 1e9
+    out.update(achieved=achieved, frac=achieved / hbm_peak,
+               alg_bytes_per_cell=bpc, steps=list(steps),
+               cells_per_launch=cells / dom_launches,
+               alg_bytes_per_launch=alg / dom_launches,
+               avg_launch_ms=dom_ms / dom_launches)
+    # measured DRAM bytes per launch, scaled from the ncu capture's bytes per
+    # cell; null once the kernel's source file has changed since the capture
+    traffic_db = {}
+    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            traffic_db = json.load(f)
+    ent = traffic_db.get(dom)
+    fresh = bool(ent) and ent.get("src") == src_digest(dom)
+    out["traffic"] = (ent["bytes_per_cell"] * cells / dom_launches) if fresh else None
+    if dom in OPS_PER_CELL:
+        keys = work["raw"][TILE_KEYS[dom]]
+        ops = cells * OPS_PER_CELL[dom] + keys * OPS_PER_KEY
+        peak = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e9
+        got = ops / (dom_ms / 1e3) / 1e9
+        out["alu_view"] = {"bound": "alu", "achieved": got, "peak": peak, "unit": "Gop/s",
+                           "frac": got / peak,
+                           "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} int lanes x "
+                                          f"{sm_mhz:.0f} MHz"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="L1024_k32_x1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="steps of the separate pass with per-kernel CUDA events")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -280,10 +380,10 @@ def main():
     rsa.rsa_kernel_stats(h)  # reset counters
     rsa.rsa_work_stats(h)
 
-    # ---- device-timed region (inputs resident: seeds + workspace) ----
+    # ---- device-timed region: the product path (graph replay, no events);
+    #      inputs resident (seeds, workspace) ----
     clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
-    rsa.rsa_profile(h, True)
     barrier()
     clocks.start()
     time.sleep(0.3)
@@ -297,13 +397,31 @@ def main():
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    kstats = rsa.rsa_kernel_stats(h)
-    work = rsa.rsa_work_stats(h)
-    rsa.rsa_profile(h, False)
+    launches = rsa.rsa_kernel_stats(h)   # launch counts of the timed region
+    rsa.rsa_work_stats(h)
+    gpu_launches = int(sum(v[1] for v in launches.values()))
     st = rsa.rsa_sample_stats(h, n)
     nj, nc = rsa.rsa_results(h, n)
     ms = max_over_ranks(ms, pg, "cuda")
     value = n * world * args.steps / (ms / 1e3)
+
+    # ---- profiled pass: the same steps with an event pair per launch ----
+    psteps = max(1, args.profile_steps)
+    rsa.rsa_profile(h, True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(psteps):
+        rsa.rsa_run_seeds(h, seeds, stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = p0.elapsed_time(p1)
+    kstats = rsa.rsa_kernel_stats(h)
+    work = rsa.rsa_work_stats(h)
+    rsa.rsa_profile(h, False)
+    pst = rsa.rsa_sample_stats(h, n)
+    pj, pc = rsa.rsa_results(h, n)
+    assert np.array_equal(pj, nj) and np.array_equal(pc, nc)
 
     # ---- end-to-end through the C ABI with host buffers ----
     nj_h = np.zeros(n, dtype=np.uint32)
@@ -335,70 +453,29 @@ def main():
             pg.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (CUDA events over the timed region) ----
+    # ---- roofline of the dominant kernel (profiled pass, CUDA events) ----
     ours = {name: v for name, v in kstats.items() if v[1] > 0}
     dom = max(ours, key=lambda nm: ours[nm][0])
-    dom_ms, dom_launches = ours[dom]
-    passes = int(np.sum(st["rounds"].astype(np.int64) + 1)) * args.steps
+    passes = int(np.sum(pst["rounds"].astype(np.int64) + 1)) * psteps
     hbm_peak, peak_kind = measured_peaks()
-    traffic_db = {}
-    tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tp):
-        with open(tp) as f:
-            traffic_db = json.load(f)
-    ent = traffic_db.get(dom)
-    fresh = bool(ent) and ent.get("src") == src_digest(dom)
-    if dom in TILE_WORK:
-        cells_key, keys_key = TILE_WORK[dom]
-        cells, keys = work[cells_key], work[keys_key]
-        ops = cells * OPS_PER_CELL[dom] + keys * OPS_PER_KEY
-        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-        sm_mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]) \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2070.0
-        peak = sm_count * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e9  # Gop/s
-        achieved = ops / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "Gop/s", "frac": achieved / peak,
-                "traffic": (ent["bytes_per_cell"] * cells / dom_launches) if fresh else None,
-                "peak_source": f"{sm_count} SMs x {ALU_LANES_PER_SM} int lanes x {sm_mhz:.0f} MHz",
-                "alg_ops_per_launch": ops / dom_launches,
-                "cells_per_launch": cells / dom_launches,
-                # one argmin code byte per cell written (cmin) or read (accept)
-                "hbm_view": {"alg_bytes_per_launch": 1.0 * cells / dom_launches,
-                             "achieved_gbs": 1.0 * cells / (dom_ms / 1e3) / 1e9,
-                             "peak_gbs": hbm_peak,
-                             "frac": 1.0 * cells / (dom_ms / 1e3) / 1e9 / hbm_peak}}
-    elif dom in BYTES_PER_CELL:
-        if dom in LINE_WORK:   # cells of segments / tiles not skipped as dead
-            ctr, share = LINE_WORK[dom]
-            cells = work["raw"][ctr] * share
-        else:
-            cells = passes * L * L
-        alg_bytes = BYTES_PER_CELL[dom] * cells
-        achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": (ent["bytes_per_cell"] * cells / dom_launches) if fresh else None,
-                "peak_source": f"{peak_kind} hbm_gbs",
-                "alg_bytes_per_launch": alg_bytes / dom_launches}
-    else:
-        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": hbm_peak,
-                "unit": "GB/s", "frac": None, "traffic": None}
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_mhz = float(json.load(open(pk))["sm_max_mhz"]) if os.path.exists(pk) else 2070.0
+    roof = roofline(dom, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz)
+    total_ms = sum(x[0] for x in ours.values())
     kernel_table = {nm: {"ms": round(v[0], 3), "launches": v[1],
-                         "share": round(v[0] / sum(x[0] for x in ours.values()), 4)}
-                    for nm, v in ours.items()}
+                         "share": round(v[0] / total_ms, 4)} for nm, v in ours.items()}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
-        rate, m, secs = cpu_oracle_rate(L, k, [int(s) for s in seeds], args.cpu_seconds, cores)
-        # the same oracle on one core, over a shorter prefix of the seeds
-        rate1, m1, secs1 = cpu_oracle_rate(L, k, [int(s) for s in seeds],
-                                           max(1.0, args.cpu_seconds / 5), 1)
+        sd = [int(s) for s in seeds] + list(range(n + 1, n + 2 * cores + 1))
+        rate, m, secs, _ = cpu_oracle_rate(L, k, sd, args.cpu_seconds, cores)
+        rate1, m1, secs1, _ = cpu_oracle_rate(L, k, sd, max(1.0, args.cpu_seconds / 5), 1)
         cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {m} seeds of {args.workload} ({secs:.1f} s on {cores} threads)",
+               "sample": sample_text(args.workload, L, k, m, secs, cores),
                "single_core": {"value": rate1, "unit": "samples/s",
-                               "sample": f"first {m1} seeds ({secs1:.1f} s on 1 thread)"}}
+                               "sample": sample_text(args.workload, L, k, m1, secs1, 1)}}
 
     out = {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
@@ -407,7 +484,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "L": L, "k": k, "samples_per_step": n,
                    "seeds": f"rank*{n}+1..rank*{n}+{n}",
-                   "l2": "working set %.1f GB per step > 129 MB L2" % (
+                   "l2": "no flush: working set %.1f GB per step > 129 MB L2" % (
                        rsa.rsa_workspace_bytes(L, k, n) / 1e9),
                    "parallelism": f"samples sharded over {world} GPU(s), no collective"},
         "sites_per_s": value * L * L,
@@ -415,8 +492,11 @@ def main():
                 "d2h_bytes_per_step": int(128 * n)},
         "plain_one_sample_per_launch": {"value": plain_rate, "unit": "samples/s",
                                         "samples": plain_n},
-        "gpu_launches": int(sum(v[1] for v in ours.values())),
+        "gpu_launches": gpu_launches,
         "roofline": roof,
+        "profiled_pass": {"steps": psteps, "ms_per_step": prof_ms / psteps,
+                          "note": "per-kernel shares and the roofline come from this pass; "
+                                  "value is timed without per-launch events"},
         "kernels": kernel_table,
         "clocks": ck,
         "cpu_baseline": cpu,

@@ -80,8 +80,10 @@ int rsa_run_keys(rsa_t *h, const uint64_t *keys, void *stream);
  *   seeds: host array of n seeds (read);  n_j, n_c: host arrays of n (written).
  * Sizes whose workspace (rsa_workspace_bytes(L, k, n)) exceeds 64 MiB are
  * rejected with RSA_EINVAL.  The first call on a device looks up the array's
- * device address (once per device, with that device current); make that
- * first call before any stream capture starts on the device.  Every call
+ * device address (once per device, with that device current, and again after
+ * that device's context has been destroyed and re-created, e.g. by
+ * cudaDeviceReset); make that first call before any stream capture starts on
+ * the device.  Every call
  * reuses the same array: a call re-initialises what it needs, but two calls
  * whose work overlaps on the GPU (other streams, other threads) race on it.
  * Synchronises `stream` like rsa_run_seeds; returns the first per-sample
@@ -138,6 +140,24 @@ int rsa_wrap_dirs(rsa_t *h, uint32_t sample, uint32_t m, uint32_t *wrap_x, uint3
 /* TEST ONLY: the accepted candidates (idx) of sample `sample` of the last run,
  * sorted ascending; *count receives n_j; at most cap values are written. */
 int rsa_accepted(rsa_t *h, uint32_t sample, uint32_t *idx, uint32_t cap, uint32_t *count);
+
+/* TEST ONLY (no counterpart in the paper): lower the caps of the device
+ * loops for later runs on this handle, so that a test can make each capped
+ * loop run out on purpose and check that the run reports it and the GPU
+ * stays usable.  0 restores a cap's default.
+ *   round_cap  greedy rounds per sample (default n_j bound + 2): a sample
+ *              still undecided after that many rounds stops with
+ *              RSA_ETIMEOUT from rsa_results;
+ *   uf_steps   steps of one union-find walk and retries of one link (default
+ *              2^20): a walk that runs out stops its probe, RSA_ETIMEOUT;
+ *   probe_cap  bisection probes per sample (default 40), RSA_ETIMEOUT;
+ *   edge_cap   contact edges stored per sample (default: the buffer's
+ *              capacity, min(2 L^2, 6 L^2/k + 4 L) + 64): more edges than
+ *              that stop the sample with RSA_ENOMEM, and nothing is written
+ *              past the cap.
+ * Every loop ends by its cap; nothing waits without a limit or faults. */
+int rsa_test_caps(rsa_t *h, uint32_t round_cap, uint32_t uf_steps, uint32_t probe_cap,
+                  uint32_t edge_cap);
 
 /* Measurement support (no counterpart in the paper).  rsa_profile(h, 1)
  * makes later runs record a CUDA event pair around every kernel launch on

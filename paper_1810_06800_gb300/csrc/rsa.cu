@@ -265,11 +265,14 @@ struct rsa {
   // chunks the previous run needed before its samples were done: the next
   // run launches that many before its first device->host check
   u32 round_chunks_hint = 1, probe_chunks_hint = 1;
+  // test-only lowered caps of the device loops (0 = default; rsa_test_caps)
+  u32 t_round = 0, t_uf = 0, t_probe = 0, t_edges = 0;
   struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
     const void* ws = nullptr;
     u32 n = 0;
     bool keys = false;
+    u32 caps[4] = {0, 0, 0, 0};  // test caps baked into the captured arguments
     unsigned long long launches[32] = {};
   } g_round, g_probe;
 };
@@ -312,6 +315,8 @@ Group group_of(rsa_t* h, u32 n) {
   g.n = n;
   g.cap_nodes = cap_nodes_of(h->L, h->k);
   g.cap_edges = cap_edges_of(h->L, h->k);
+  g.uf_cap = h->t_uf ? h->t_uf : UF_CAP;
+  g.edge_limit = h->t_edges ? std::min(h->t_edges, g.cap_edges) : g.cap_edges;
   g.LL = (u64)h->L * h->L;
   g.occ = reinterpret_cast<u8*>(b + l.occ);
   g.owner = reinterpret_cast<u32*>(b + l.owner);
@@ -440,7 +445,9 @@ int run_chunk(rsa_t* h, rsa_t::GraphSlot& gs, cudaStream_t stream, u32 n, B body
     body(stream);
     return launch_check("chunk launches");
   }
-  if (!(gs.exec && gs.ws == h->ws && gs.n == n && gs.keys == h->with_keys)) {
+  const u32 caps[4] = {h->t_round, h->t_uf, h->t_probe, h->t_edges};
+  if (!(gs.exec && gs.ws == h->ws && gs.n == n && gs.keys == h->with_keys &&
+        std::memcmp(gs.caps, caps, sizeof(caps)) == 0)) {
     drop_graph(gs);
     if (!h->cap_stream)
       CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
@@ -467,6 +474,7 @@ int run_chunk(rsa_t* h, rsa_t::GraphSlot& gs, cudaStream_t stream, u32 n, B body
     gs.ws = h->ws;
     gs.n = n;
     gs.keys = h->with_keys;
+    std::memcpy(gs.caps, caps, sizeof(caps));
   }
   CUDA_TRY(cudaGraphLaunch(gs.exec, stream));
   for (int i = 0; i < KD_COUNT; ++i) h->prof.launches[i] += gs.launches[i];
@@ -537,7 +545,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   }
   // every round accepts at least the smallest live key, so n_j + 1 rounds
   // always suffice
-  const u32 round_cap = cap_nodes_of(h->L, h->k) + 2;
+  const u32 round_cap = h->t_round ? h->t_round : cap_nodes_of(h->L, h->k) + 2;
+  const u32 probe_cap = h->t_probe ? h->t_probe : PROBE_CAP;
   // one chunk = ROUND_CHECK greedy rounds; k_round_end counts the samples
   // still active after each round into d_counter
   u32* occT = reinterpret_cast<u32*>(b + l.occT);
@@ -621,11 +630,11 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
       if (cudaMemsetAsync(d_counter + 1, 0, 4, st) != cudaSuccess) body_rc = RSA_ECUDA;
       launch(h, KD_PROBE_COPY, k_probe_copy, dim3(copy_bx, n), dim3(256), 0, st, g);
       launch(h, KD_PROBE, k_probe, dim3(probe_bx, n), dim3(256), 0, st, g);
-      launch(h, KD_DECIDE, k_search_decide, dim3(n), dim3(256), 0, st, g, (u32)PROBE_CAP,
+      launch(h, KD_DECIDE, k_search_decide, dim3(n), dim3(256), 0, st, g, probe_cap,
              d_counter + 1);
     }
   };
-  for (u32 chunks = 0; chunks * PROBE_CHECK < PROBE_CAP + PROBE_CHECK;) {
+  for (u32 chunks = 0; chunks * PROBE_CHECK < probe_cap + PROBE_CHECK;) {
     const u32 burst = chunks == 0 ? h->probe_chunks_hint : 1;
     for (u32 i = 0; i < burst; ++i, ++chunks)
       if ((rc = run_chunk(h, h->g_probe, stream, n, probes))) return rc;
@@ -677,22 +686,47 @@ static __device__ __align__(256) unsigned char g_static_ws[STATIC_WS_BYTES];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[MAX_DEVICES] = {};
+unsigned long long g_static_ctx[MAX_DEVICES] = {};
+
+// Unique id of the current CUDA context (cuCtxGetId, reached through the
+// runtime's driver entry-point table so the library does not link libcuda),
+// or 0 if there is none or the driver lacks the call.
+unsigned long long current_context_id() {
+  typedef int (*ctx_id_fn)(void*, unsigned long long*);
+  static ctx_id_fn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<ctx_id_fn>(f);
+  }();
+  unsigned long long id = 0;
+  if (!fn || fn(nullptr, &id) != 0) return 0;
+  return id;
+}
 
 // Device address of g_static_ws on the current device, looked up once per
-// device (with that device current).  In host code the symbol itself is only
-// a host-side stand-in, never a device address.
+// device (with that device current) and again whenever that device's context
+// has changed since (a context destroyed by cudaDeviceReset and created anew
+// may place the array elsewhere).  In host code the symbol itself is only a
+// host-side stand-in, never a device address.
 int static_workspace(void** out) {
   int dev = -1;
   CUDA_TRY(cudaGetDevice(&dev));
   if (dev < 0 || dev >= MAX_DEVICES) return fail(RSA_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_static_ptr[dev] || ctx == 0 || ctx != g_static_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_ws);
     if (e != cudaSuccess || !p)
       return fail(RSA_ECUDA, std::string("cudaGetSymbolAddress(static workspace): ") +
                                  cudaGetErrorString(e));
     g_static_ptr[dev] = p;
+    g_static_ctx[dev] = current_context_id();  // the lookup made the context current
   }
   *out = g_static_ptr[dev];
   return 0;
@@ -933,6 +967,16 @@ int rsa_bind_workspace(rsa_t* h, void* dev_ptr, uint64_t bytes) {
     return fail(RSA_EINVAL, "workspace must be 256-byte aligned");
   h->bound_ptr = dev_ptr;
   h->bound_bytes = dev_ptr ? bytes : 0;
+  return 0;
+}
+
+int rsa_test_caps(rsa_t* h, uint32_t round_cap, uint32_t uf_steps, uint32_t probe_cap,
+                  uint32_t edge_cap) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  h->t_round = round_cap;
+  h->t_uf = uf_steps;
+  h->t_probe = probe_cap;
+  h->t_edges = edge_cap;
   return 0;
 }
 

@@ -105,7 +105,7 @@ __global__ void k_cfg_union(Group g, u32 s) {
     const Edge e = E[i];
     if (e.time > T) continue;
     u32 mis = 0;
-    if (uf_union(W, e.m1, e.m2, e.dxy, &capped, &mis))
+    if (uf_union(W, e.m1, e.m2, e.dxy, &capped, g.uf_cap, &mis))
       dirs |= ((mis & 0xFFFFu) ? 1u : 0u) | ((mis >> 16) ? 2u : 0u);
   }
   if (capped) dirs |= CFG_CAPPED;
@@ -124,7 +124,7 @@ __global__ void k_cfg_count(Group g, u32 s) {
   for (u32 m = blockIdx.x * blockDim.x + threadIdx.x; m < nn; m += gridDim.x * blockDim.x) {
     if (K[m] > T) continue;
     u32 ox, oy;
-    const u32 r = uf_find(W, m, &ox, &oy, &capped);
+    const u32 r = uf_find(W, m, &ox, &oy, &capped, g.uf_cap);
     atomicAdd(&size[r], 1u);
   }
   if (__any_sync(FULL, capped) && (threadIdx.x & 31) == 0) atomicOr(&st.wdirs, CFG_CAPPED);

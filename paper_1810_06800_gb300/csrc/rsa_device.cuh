@@ -91,6 +91,8 @@ static_assert(sizeof(SampleState) == 128, "SampleState is 128 bytes");
 struct Group {         // one batch of samples sharing (L, k)
   u32 L, k, n;
   u32 cap_nodes, cap_edges;
+  u32 uf_cap;          // steps of one union-find walk or link retry loop
+  u32 edge_limit;      // contact edges stored per sample (<= cap_edges)
   u64 LL;
   u8* occ;             // [n][L][L]   1 = occupied
   u32* owner;          // [n][L][L]   node id (| OWN_V if vertical) or NONE32

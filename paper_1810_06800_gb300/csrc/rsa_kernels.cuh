@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(EDGES_THREADS) k_edges(Group g) {
       basei = __shfl_sync(FULL, basei, leader);
       if (emit) {
         const u32 e = basei + __popc(mask & ((1u << lane) - 1u));
-        if (e < g.cap_edges) {
+        if (e < g.edge_limit) {
           Edge ed;
           const u32 ma = a & ~OWN_V, mb = b & ~OWN_V;
           ed.time = max(nkey[ma], nkey[mb]);
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(1024) k_bucket(Group g) {
   __shared__ u32 he[NBKT], hn[NBKT], ce[NBKT], cn[NBKT];
   const u32 s = blockIdx.x;
   SampleState& st = g.st[s];
-  const u32 ne = min(st.n_edges, g.cap_edges), nn = min(st.n_nodes, g.cap_nodes);
+  const u32 ne = min(st.n_edges, g.edge_limit), nn = min(st.n_nodes, g.cap_nodes);
   const Edge* E = g.edges + (size_t)s * g.cap_edges;
   Edge* E2 = g.edges_b + (size_t)s * g.cap_edges;
   const u64* K = g.node_key + (size_t)s * g.cap_nodes;
@@ -402,14 +402,14 @@ __device__ __forceinline__ u64 uf_pack(u32 p, u32 dx, u32 dy) {
   return (u64)p | ((u64)(dx & 0xFFFFu) << 32) | ((u64)(dy & 0xFFFFu) << 48);
 }
 
-constexpr u32 UF_CAP = 1u << 20;
+constexpr u32 UF_CAP = 1u << 20;  // default walk / retry cap (Group::uf_cap)
 
 // Root of x and x's offset from it.  Path halving by CAS; a failed CAS is
 // harmless because every stored (parent, offset) pair stays a true ancestor
 // relation.  Loads bypass L1 (other SMs write these words).
-__device__ __forceinline__ u32 uf_find(u64* W, u32 x, u32* ox, u32* oy, bool* capped) {
+__device__ __forceinline__ u32 uf_find(u64* W, u32 x, u32* ox, u32* oy, bool* capped, u32 cap) {
   u32 sx = 0, sy = 0;
-  for (u32 it = 0; it < UF_CAP; ++it) {
+  for (u32 it = 0; it < cap; ++it) {
     const u64 wx = __ldcg(W + x);
     const u32 p = (u32)wx;
     if (p == x) {
@@ -439,12 +439,13 @@ __device__ __forceinline__ u32 uf_find(u64* W, u32 x, u32* ox, u32* oy, bool* ca
 // mismatch (x in bits 0-15, y in 16-31, modulo 2^16).  Roots are linked
 // larger-id under smaller-id, so the forest stays acyclic under concurrent
 // unions.
-__device__ bool uf_union(u64* W, u32 m1, u32 m2, u32 dxy, bool* capped, u32* mis = nullptr) {
+__device__ bool uf_union(u64* W, u32 m1, u32 m2, u32 dxy, bool* capped, u32 cap,
+                         u32* mis = nullptr) {
   const u32 dx = dxy & 0xFFFFu, dy = dxy >> 16;
-  for (u32 it = 0; it < UF_CAP; ++it) {
+  for (u32 it = 0; it < cap; ++it) {
     u32 o1x, o1y, o2x, o2y;
-    const u32 r1 = uf_find(W, m1, &o1x, &o1y, capped);
-    const u32 r2 = uf_find(W, m2, &o2x, &o2y, capped);
+    const u32 r1 = uf_find(W, m1, &o1x, &o1y, capped, cap);
+    const u32 r2 = uf_find(W, m2, &o2x, &o2y, capped, cap);
     if (*capped) return false;
     // lifted position of r2 minus r1
     const u32 Dx = o1x + dx - o2x, Dy = o1y + dy - o2y;
@@ -522,7 +523,7 @@ __global__ void __launch_bounds__(256, 8) k_probe(Group g) {
   for (u32 i = e0 + blockIdx.x * blockDim.x + threadIdx.x; i < e1; i += stride) {
     const Edge e = E[i];
     if (e.time > mid || (lo_valid && e.time <= lo)) continue;
-    if (uf_union(Wd, e.m1, e.m2, e.dxy, &capped)) wrap = true;
+    if (uf_union(Wd, e.m1, e.m2, e.dxy, &capped, g.uf_cap)) wrap = true;
   }
   const bool bw = __syncthreads_or(wrap);
   const bool bc = __syncthreads_or(capped);

@@ -22,7 +22,7 @@ _NAMES = {RSA_EINVAL: "RSA_EINVAL", RSA_ENOMEM: "RSA_ENOMEM", RSA_ECUDA: "RSA_EC
 SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_run_static",
            "rsa_results",
            "rsa_sample_stats", "rsa_contacts", "rsa_cluster_sizes", "rsa_wrap_dirs", "rsa_accepted",
-           "rsa_workspace_bytes", "rsa_bind_workspace",
+           "rsa_workspace_bytes", "rsa_bind_workspace", "rsa_test_caps",
            "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
@@ -62,6 +62,7 @@ def load():
     lib.rsa_accepted.argtypes = [vp, u32, vp, u32, ctypes.POINTER(u32)]
     lib.rsa_workspace_bytes.argtypes = [u32, u32, u32, ctypes.POINTER(u64)]
     lib.rsa_bind_workspace.argtypes = [vp, vp, u64]
+    lib.rsa_test_caps.argtypes = [vp, u32, u32, u32, u32]
     lib.rsa_destroy.argtypes = [vp]
     lib.rsa_destroy.restype = None
     lib.rsa_profile.argtypes = [vp, ip]
@@ -193,6 +194,12 @@ def rsa_bind_workspace(h, tensor_or_ptr, nbytes: int | None = None):
     else:
         ptr = int(tensor_or_ptr)
     return _check(load().rsa_bind_workspace(h, ctypes.c_void_p(ptr), int(nbytes)))
+
+
+def rsa_test_caps(h, round_cap: int = 0, uf_steps: int = 0, probe_cap: int = 0,
+                  edge_cap: int = 0):
+    """TEST ONLY: lower the device loop caps of later runs (0 = default)."""
+    return _check(load().rsa_test_caps(h, round_cap, uf_steps, probe_cap, edge_cap))
 
 
 def rsa_profile(h, enable: bool = True):
