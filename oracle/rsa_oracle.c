@@ -82,16 +82,13 @@ static void orc_cell(uint32_t L, uint32_t idx, uint32_t i, uint32_t *y, uint32_t
     else        { *y = (y0 + i) % L; *x = x0; }
 }
 
-/* Scan the 2L^2 candidates in ascending key order; accept a candidate iff
- * its k cells are free.  accepted[] receives the accepted idx in scan order.
- * Returns n_j, or -1 if two keys are equal (the order would be undefined). */
-int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
-                    uint32_t *accepted, uint8_t *occ)
+/* Sort the n = 2L^2 (key, idx) pairs and scan them in ascending key order,
+ * accepting a candidate iff its k cells are free.  accepted[] receives the
+ * accepted idx in scan order.  Returns n_j, or -1 if two keys are equal (the
+ * order would be undefined).  Frees p. */
+static int64_t orc_scan_pairs(uint32_t L, uint32_t k, orc_pair *p, uint64_t n,
+                              uint32_t *accepted, uint8_t *occ)
 {
-    uint64_t n = 2ULL * L * L;
-    orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
-    if (!p) return -2;
-    for (uint64_t i = 0; i < n; ++i) { p[i].key = keys[i]; p[i].idx = (uint32_t)i; }
     qsort(p, n, sizeof(orc_pair), orc_cmp);
     for (uint64_t i = 1; i < n; ++i)
         if (p[i].key == p[i - 1].key) { free(p); return -1; }
@@ -112,6 +109,30 @@ int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
     }
     free(p);
     return nj;
+}
+
+/* Scan the 2L^2 candidates of caller-given keys (Sec. II.B). */
+int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
+                    uint32_t *accepted, uint8_t *occ)
+{
+    uint64_t n = 2ULL * L * L;
+    orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
+    if (!p) return -2;
+    for (uint64_t i = 0; i < n; ++i) { p[i].key = keys[i]; p[i].idx = (uint32_t)i; }
+    return orc_scan_pairs(L, k, p, n, accepted, occ);
+}
+
+/* The same scan for the seeded priorities of oracle_keys, with the pairs
+ * formed straight from oracle_key: no separate array of 2L^2 keys, so the
+ * largest lattices (L = 32768: 34 GB of pairs) fit in host memory. */
+int64_t oracle_scan_seed(uint32_t L, uint32_t k, uint64_t seed, uint32_t *accepted,
+                         uint8_t *occ)
+{
+    uint64_t n = 2ULL * L * L, b = oracle_base(seed);
+    orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
+    if (!p) return -2;
+    for (uint64_t i = 0; i < n; ++i) { p[i].key = oracle_key(b, i); p[i].idx = (uint32_t)i; }
+    return orc_scan_pairs(L, k, p, n, accepted, occ);
 }
 
 /* ---- union-find with displacement vectors (Sec. II.C, II.D) ------------ */

@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc", "rsa.cu")
 DEPS = [SRC, os.path.join(HERE, "csrc", "rsa_kernels.cuh"),
         os.path.join(HERE, "csrc", "rsa_device.cuh"), os.path.join(HERE, "csrc", "rsa_tile.cuh"),
-        os.path.join(HERE, "csrc", "rsa_line.cuh"), os.path.join(HERE, "csrc", "rsa_config.cuh"),
+        os.path.join(HERE, "csrc", "rsa_line.cuh"), os.path.join(HERE, "csrc", "rsa_lwin.cuh"),
+        os.path.join(HERE, "csrc", "rsa_config.cuh"),
         os.path.join(os.path.dirname(HERE), "include", "rsa.h")]
 LIB = os.path.join(HERE, "_lib", "librsa_gb300.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",

@@ -20,6 +20,7 @@
 #include "rsa_kernels.cuh"
 #include "rsa_tile.cuh"
 #include "rsa_line.cuh"
+#include "rsa_lwin.cuh"
 #include "rsa_config.cuh"
 
 using namespace rsak;
@@ -49,7 +50,7 @@ constexpr size_t SMEM_BUDGET = 160 * 1024;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t occ, occw, occT, cB, code16, code16T, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
+  size_t occ, occw, occT, cB, code16, code16T, cH, cV, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
       ebkt, nkey_b, nbkt, st, seeds, counters, work, keys,
       scratch, total;
 };
@@ -58,6 +59,13 @@ struct Geometry {
   bool tile;                    // power-of-two k <= 32 and L % 32 == 0
   bool line;                    // 32 <= k <= LINE_KMAX, L % 32 == 0, not tile
   LineCfg lc;
+  // long-k lines made of whole k-blocks and whole CTA spans (rsa_lwin.cuh),
+  // used for seeded priorities; caller priorities keep the lc kernels
+  bool lw;
+  LwinCfg lw_cfg;
+  u32 lw_C;                     // cells per thread of k_lwin
+  LineCfg lw_acc;               // acceptance over the same spans
+  size_t lw_acc_smem;
   size_t line_smem, line_acc_smem, line_codes_smem;
   TileCfg tc;                   // (items filled per run)
   RowCfg row;
@@ -103,6 +111,21 @@ Geometry plan(u32 L, u32 k) {
     G.line_smem = line_smem_bytes(G.lc.nmax, S, k, G.lc.compact != 0);
     G.line_acc_smem = line_smem_bytes(G.lc.nmax, S, k);
     G.line_codes_smem = line_codes_smem_bytes(G.lc.nmax);
+    const u32 P = std::min<u32>(L, 4096), C = P / LW_THREADS;
+    G.lw = P % LW_THREADS == 0 && C >= 1 && C <= 16 && (C & (C - 1)) == 0 && L % P == 0 &&
+           P % k == 0 && k % C == 0 && L / P <= 8;
+    if (G.lw) {
+      G.lw_cfg.P = P;
+      G.lw_cfg.nc = L / P;
+      G.lw_cfg.T = L / 32;
+      G.lw_C = C;
+      G.lw_acc.S = P;
+      G.lw_acc.nseg = L / P;
+      G.lw_acc.nmax = P + k - 1;
+      G.lw_acc.T = L / 32;
+      G.lw_acc.compact = 0;
+      G.lw_acc_smem = line_codes_smem_bytes(G.lw_acc.nmax);
+    }
   }
   // ---- row pass: one warp per (row, segment) ----
   RowCfg& r = G.row;
@@ -171,18 +194,26 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
     return at;
   };
   const bool bits = G.tile || G.line;
+  const bool lw = G.lw && !with_keys;        // argmin-offset round (rsa_lwin.cuh)
+  const bool lold = G.line && !lw;           // 8-byte minima round (rsa_line.cuh)
   l.occ = take(bits ? 0 : n * LL);
   l.occw = take(bits ? n * LL / 8 : 0);
   l.occT = take(G.line ? n * LL / 8 : 0);
-  l.cB = take(G.line ? n * LL * 8 : 0);
+  l.cB = take(lold ? n * LL * 8 : 0);
   l.code16 = take(G.line ? n * LL * 2 : 0);
   l.code16T = take(G.line ? n * LL * 2 : 0);
-  // dead flags: per 32 x 32 tile (tile path); per line segment of each
-  // orientation, then per 32 x 32 code tile (long-k path)
+  l.cH = take(lw ? n * LL * 2 : 0);
+  l.cV = take(lw ? n * LL * 2 : 0);
+  // dead flags: per 32 x 32 tile (tile path); per line segment (or span) of
+  // each orientation, then per 32 x 32 code tile (long-k path)
+  // (32 x 16 code strips on the argmin-offset path)
+  const u32 nseg = lw ? G.lw_cfg.nc : G.lc.nseg;
+  const size_t ncode = lw ? 2ull * G.tc.T2 : G.tc.T2;
   l.dead = take(G.tile ? (size_t)n * G.tc.T2
-                       : G.line ? (size_t)n * (2ull * L * G.lc.nseg + G.tc.T2) : 0);
+                       : G.line ? (size_t)n * (2ull * L * nseg + ncode) : 0);
   l.owner = take(n * LL * 4);
-  l.cmin = take(n * LL * (G.tile ? 1 : 8));  // tile path: one argmin code byte per cell
+  // tile path: one argmin code byte per cell; none on the argmin-offset path
+  l.cmin = take(n * LL * (G.tile ? 1 : lw ? 0 : 8));
   l.base = take((size_t)n * 8);
   l.node_key = take(n * cn * 8);
   l.node_idx = take(n * cn * 4);
@@ -216,13 +247,14 @@ int set_smem(F* fn, size_t bytes) {
 enum Kind {
   KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
   KD_LINE_CMIN_H, KD_LINE_CMIN_V, KD_LINE_COMBINE, KD_LINE_ACCEPT_H, KD_LINE_ACCEPT_V,
-  KD_LINE_CODES,
+  KD_LINE_CODES, KD_LWIN_H, KD_LWIN_V, KD_LCOMB,
   KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE, KD_COUNT
 };
 const char* const kKindNames[KD_COUNT] = {
     "k_init",         "k_row_cmin",    "k_col_cmin",   "k_row_accept", "k_col_accept",
     "k_tile_cmin",    "k_tile_accept", "k_line_cmin_h", "k_line_cmin_v", "k_line_combine",
-    "k_line_accept_h", "k_line_accept_v", "k_line_codes", "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
+    "k_line_accept_h", "k_line_accept_v", "k_line_codes", "k_lwin_h", "k_lwin_v", "k_lcomb",
+    "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
     "k_probe_copy",   "k_probe",       "k_search_decide"};
 
 // Optional per-kernel timing with CUDA events recorded around each launch
@@ -368,6 +400,55 @@ void launch(rsa_t* h, int kind, K kernel, dim3 grid, dim3 block, size_t smem, cu
   p.launches[kind] += 1;
 }
 
+// As launch(), for a kernel launched in thread-block clusters of
+// cluster_x CTAs along x.  Returns the launch's error.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(rsa_t* h, int kind, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                           size_t smem, cudaStream_t st, u32 cluster_x, Args... args) {
+  Prof& p = h->prof;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (p.on) {
+    size_t i = p.kinds.size();
+    e0 = prof_event(p, 2 * i);
+    e1 = prof_event(p, 2 * i + 1);
+    if (e0 && e1) {
+      cudaEventRecord(e0, st);
+      p.kinds.push_back(kind);
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster_x;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  if (e0 && e1) cudaEventRecord(e1, st);
+  p.launches[kind] += 1;
+  return e;
+}
+
+template <int F>
+cudaError_t launch_lwin(rsa_t* h, Group g, const Geometry& G, const u32* occw, const u32* occT,
+                        u16* out, u8* lflag, u32 n, cudaStream_t st) {
+  const dim3 grid(g.L * G.lw_cfg.nc, n), block(LW_THREADS);
+  const int kind = F == 0 ? KD_LWIN_H : KD_LWIN_V;
+  const u32 nc = G.lw_cfg.nc;
+  switch (G.lw_C) {
+    case 1: return launch_cluster(h, kind, k_lwin<F, 1>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+    case 2: return launch_cluster(h, kind, k_lwin<F, 2>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+    case 4: return launch_cluster(h, kind, k_lwin<F, 4>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+    case 8: return launch_cluster(h, kind, k_lwin<F, 8>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+    default: return launch_cluster(h, kind, k_lwin<F, 16>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+  }
+}
+
 int launch_check(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(RSA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -498,6 +579,10 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   u32* d_counter = reinterpret_cast<u32*>(b + l.counters);
   const u64 LL = g.LL;
 
+  // long-k lines made of whole k-blocks run the argmin-offset round for
+  // seeded priorities; caller priorities cannot be inverted
+  const bool use_lw = G.lw && !h->with_keys;
+  const u32 line_nseg = use_lw ? G.lw_cfg.nc : G.lc.nseg;
   CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, (size_t)n * 8, cudaMemcpyHostToDevice, stream));
   if (keys)
     CUDA_TRY(cudaMemcpyAsync(b + l.keys, keys, 2 * LL * 8, cudaMemcpyHostToDevice, stream));
@@ -507,7 +592,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   } else if (G.line) {
     CUDA_TRY(cudaMemsetAsync(b + l.occw, 0, (size_t)n * LL / 8, stream));
     CUDA_TRY(cudaMemsetAsync(b + l.occT, 0, (size_t)n * LL / 8, stream));
-    CUDA_TRY(cudaMemsetAsync(b + l.dead, 0, (size_t)n * (2ull * h->L * G.lc.nseg + G.tc.T2),
+    const size_t ncode = use_lw ? 2ull * G.tc.T2 : G.tc.T2;
+    CUDA_TRY(cudaMemsetAsync(b + l.dead, 0, (size_t)n * (2ull * h->L * line_nseg + ncode),
                              stream));
   } else {
     CUDA_TRY(cudaMemsetAsync(g.occ, 0, (size_t)n * LL, stream));
@@ -524,8 +610,10 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
     if ((rc = set_smem(k_line_cmin<1>, G.line_smem))) return rc;
     if ((rc = set_smem(k_line_accept<0>, G.line_acc_smem))) return rc;
     if ((rc = set_smem(k_line_accept<1>, G.line_acc_smem))) return rc;
-    if ((rc = set_smem(k_line_accept_codes<0>, G.line_codes_smem))) return rc;
-    if ((rc = set_smem(k_line_accept_codes<1>, G.line_codes_smem))) return rc;
+    const size_t acc_smem = use_lw ? std::max(G.lw_acc_smem, G.line_codes_smem) : G.line_codes_smem;
+    if ((rc = set_smem(k_line_accept_codes<0>, acc_smem))) return rc;
+    if ((rc = set_smem(k_line_accept_codes<1>, acc_smem))) return rc;
+    if ((rc = set_smem(k_lcomb, sizeof(LcombSmem)))) return rc;
   } else if (!G.tile) {
     if ((rc = set_smem(k_row<0>, G.row_smem))) return rc;
     if ((rc = set_smem(k_row<1>, G.row_smem))) return rc;
@@ -557,6 +645,25 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
       if (cudaMemsetAsync(d_counter, 0, 4, st) != cudaSuccess) body_rc = RSA_ECUDA;
       if (G.tile) {
         if (launch_tile(h, g, tc, occw, dead, tgrid, st)) body_rc = RSA_EINVAL;
+      } else if (use_lw) {
+        u8* lflag = dead;                                          // [n][2][L][nc]
+        u8* cdead = dead + (size_t)n * 2 * h->L * line_nseg;       // [n][T^2]
+        u16* cH = reinterpret_cast<u16*>(b + l.cH);
+        u16* cV = reinterpret_cast<u16*>(b + l.cV);
+        u16* c16 = reinterpret_cast<u16*>(b + l.code16);
+        u16* c16T = reinterpret_cast<u16*>(b + l.code16T);
+        if (launch_lwin<0>(h, g, G, occw, occT, cH, lflag, n, st) != cudaSuccess) body_rc = RSA_ECUDA;
+        if (launch_lwin<1>(h, g, G, occw, occT, cV, lflag, n, st) != cudaSuccess) body_rc = RSA_ECUDA;
+        launch(h, KD_LCOMB, k_lcomb, dim3((2 * G.tc.T2 + LC_WARPS - 1) / LC_WARPS, n),
+               dim3(LC_WARPS * 32), sizeof(LcombSmem), st, g, (const u16*)cH, (const u16*)cV, c16,
+               c16T, cdead);
+        const dim3 ag(h->L * line_nseg, n);
+        launch(h, KD_LINE_ACCEPT_H, k_line_accept_codes<0>, ag, dim3(LINE_THREADS),
+               G.lw_acc_smem, st, g, G.lw_acc, occw, occT, (const u16*)c16, (const u16*)c16T,
+               (const u8*)lflag);
+        launch(h, KD_LINE_ACCEPT_V, k_line_accept_codes<1>, ag, dim3(LINE_THREADS),
+               G.lw_acc_smem, st, g, G.lw_acc, occw, occT, (const u16*)c16, (const u16*)c16T,
+               (const u8*)lflag);
       } else if (G.line) {
         const dim3 lg(h->L * G.lc.nseg, n), tg(G.tc.T2, n);
         u8* ldead = dead;                                          // [n][2][L][nseg]

@@ -1,0 +1,378 @@
+// rsa_lwin.cuh -- round kernels of the long-k path for lattices whose lines
+// split into whole k-blocks (L a multiple of k and of the CTA span P), sm_103a.
+//
+// One round, with argmin offsets instead of 8-byte minima:
+//   k_lwin<0>   along each row y: for every cell, the live horizontal
+//               candidate of smallest priority among those covering it, as
+//               its offset d = cell - anchor (0 .. k-1) or CODE_NONE;
+//   k_lwin<1>   the same along each column (rows of the transposed
+//               occupancy), stored transposed;
+//   k_lcomb     per cell, the smaller of the two winners' priorities (both
+//               recomputed from their anchors) picks the final 2-byte code,
+//               written in both layouts (32 x 16 strips, one warp each);
+//   k_line_accept_codes<F>  acceptance from code runs (rsa_line.cuh).
+//
+// k_lwin is van Herk / Gil-Werman with blocks of k cells aligned on the line
+// (L is a multiple of k, so the blocks tile the torus): the window of cell x
+// in block b at offset j is the suffix minimum of block b-1 from offset j+1
+// and the prefix minimum of block b up to j (the whole of block b if
+// j = k-1).  A line is cut into nc = L / P spans of P = 256 C cells, one CTA
+// each, launched as one thread-block cluster per line.  Thread t holds the C
+// consecutive candidates of its chunk in registers: liveness from the staged
+// occupancy words (a candidate is live iff the next occupied cell is at
+// least k ahead), splitmix64 priorities of the live ones, in-chunk prefix and
+// suffix minima, and segmented block scans of the chunk minima within each
+// k-block.  Suffix minima go to shared memory; the window of a cell whose
+// block b-1 lies in the previous span reads them from that CTA's shared
+// memory over the cluster (distributed shared memory), so no priority is
+// computed twice.  The winner's offset comes from inverting its priority
+// (splitmix64 is a bijection), once per change of the window minimum along
+// the chunk.
+//
+// A span with no live anchor has no live anchor in any later round: it is
+// flagged and skips hashing and scans; once it and the span before it are
+// both flagged, its outputs (written as "none" in the round that made them
+// so) are not touched again.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "rsa_line.cuh"
+
+namespace rsak {
+
+constexpr u32 LW_THREADS = 256;
+constexpr u32 LW_INF = 0xFFFFFFFFu;
+
+struct LwinCfg {
+  u32 P;   // cells of a line per CTA: 256 * C, a multiple of k and of 32
+  u32 nc;  // CTAs per line (cluster size), L = nc * P, nc <= 8
+  u32 T;   // occupancy words per line, L / 32
+};
+
+// Exclusive segmented scan (min) of one value per thread over the block,
+// in thread order (BWD: descending).  Segments are runs of m consecutive
+// threads starting at multiples of m.  `buf` holds 256 u64 of scratch.
+template <bool BWD>
+__device__ __forceinline__ u64 lw_seg_scan_excl(u64 a, u32 m, u64* buf, u64* wv, u32* wf) {
+  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the thread opens a segment in scan order (its first thread)
+  const bool head = BWD ? (tid % m == m - 1) : (tid % m == 0);
+  u64 v = a;
+  bool f = head;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const u64 o = BWD ? __shfl_down_sync(FULL, v, d) : __shfl_up_sync(FULL, v, d);
+    const bool of = BWD ? __shfl_down_sync(FULL, f, d) : __shfl_up_sync(FULL, f, d);
+    const bool ok = BWD ? lane + d < 32 : (int)lane >= d;
+    if (ok) {
+      if (!f) v = tmin(v, o);
+      f = f || of;
+    }
+  }
+  // totals of each warp (its last thread in scan order)
+  if (lane == (BWD ? 0u : 31u)) {
+    wv[warp] = v;
+    wf[warp] = f;
+  }
+  __syncthreads();
+  u64 incl = v;
+  if (!f) {
+    // carry from the warps before this one in scan order, up to a head
+    if (BWD) {
+      for (u32 w2 = warp + 1; w2 < LW_THREADS / 32; ++w2) {
+        incl = tmin(incl, wv[w2]);
+        if (wf[w2]) break;
+      }
+    } else {
+      for (int w2 = (int)warp - 1; w2 >= 0; --w2) {
+        incl = tmin(incl, wv[w2]);
+        if (wf[w2]) break;
+      }
+    }
+  }
+  buf[tid] = incl;
+  __syncthreads();
+  u64 ex = KEY_NONE;
+  if (!head) ex = buf[BWD ? tid + 1 : tid - 1];
+  __syncthreads();  // buf and the warp totals are reused by the next scan
+  return ex;
+}
+
+// F = 0: rows y of occw, offsets to cH[y][.]; F = 1: columns x (rows of the
+// transposed occT), offsets to cV[x][.].  lflag[((s * 2 + F) * L + line) *
+// nc + r] bit 0: span r of the line has no live anchor (stays so).
+template <int F, int C>
+__global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const u32* occw,
+                                                     const u32* occT, u16* cout, u8* lflag) {
+  namespace cg = cooperative_groups;
+  __shared__ u64 Qs[C][LW_THREADS];      // suffix minimum of chunk t, element e at [e][t]
+  __shared__ u32 w[LW_THREADS + 2];      // staged occupancy words
+  __shared__ u32 nw[LW_THREADS + 2];     // first occupied position at / after word i
+  __shared__ u64 sbuf[LW_THREADS];
+  __shared__ u64 wv[LW_THREADS / 32];
+  __shared__ u32 wf[LW_THREADS / 32];
+  __shared__ u32 wmin[LW_THREADS / 32];
+  cg::cluster_group cl = cg::this_cluster();
+  const u32 nc = lc.nc, r = cl.block_rank();
+  const u32 line = blockIdx.x / nc, s = blockIdx.y;
+  if (g.st[s].done) return;  // the same for every CTA of the cluster
+  const u32 L = g.L, k = g.k, T = lc.T, P = lc.P;
+  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 rp = r == 0 ? nc - 1 : r - 1;
+  u8* fl = lflag + ((size_t)(s * 2 + F) * L + line) * nc;
+  const bool own_dead = (fl[r] & 1u) != 0, prev_dead = (fl[rp] & 1u) != 0;
+  const u32 x0 = r * P;
+  const u32 q0 = tid * C;               // first cell of this thread's chunk (relative to x0)
+  const u64 zb = g.base[s] + SM_GAMMA;  // splitmix64 input of candidate idx: zb + gamma idx
+  u64 v[C];
+  bool any = false;
+  if (!own_dead) {
+    // occupancy words of [x0, x0 + P + k - 1), around the torus
+    const u32 nwords = (P + k + 30) / 32;  // <= 256: P, k <= 4096
+    const u32* bits = (F == 0 ? occw : occT) + ((size_t)s * L + line) * T;
+    u32 fst = LW_INF;
+    if (tid < nwords) {
+      u32 wi = x0 / 32 + tid;
+      while (wi >= T) wi -= T;
+      const u32 wd = bits[wi];
+      w[tid] = wd;
+      if (wd) fst = tid * 32 + __ffs(wd) - 1;
+    }
+    // nw[i] = min over words j >= i of their first occupied position
+    u32 sm = fst;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const u32 o = __shfl_down_sync(FULL, sm, d);
+      if (lane + d < 32) sm = min(sm, o);
+    }
+    if (lane == 0) wmin[warp] = sm;
+    __syncthreads();
+    for (u32 w2 = warp + 1; w2 < LW_THREADS / 32; ++w2) sm = min(sm, wmin[w2]);
+    nw[tid] = sm;
+    if (tid == 0) nw[LW_THREADS] = LW_INF;
+    __syncthreads();
+    // the chunk's candidates.  k > 32, so a candidate at q is live iff no
+    // cell of its own word from q on is occupied (q is past the word's last
+    // occupied bit) and the first occupied cell after that word is at least
+    // k ahead: an interval e_lo <= e <= e_hi of the chunk's offsets
+    const u32 wi = q0 >> 5, rb = q0 & 31u;  // C divides 32: one word holds the chunk
+    const u32 wd = w[wi], nxtw = nw[wi + 1];
+    const int e_lo = wd ? (int)(31 - __clz(wd)) - (int)rb + 1 : 0;
+    const int e_hi = nxtw == LW_INF ? C : (int)nxtw - (int)k - (int)q0;
+    const u64 zstep = F == 0 ? SM_GAMMA : SM_GAMMA * (u64)L;
+    u64 z = zb + SM_GAMMA * (F == 0 ? (u64)line * L + x0 + q0
+                                    : g.LL + (u64)(x0 + q0) * L + line);
+    u64 agg = KEY_NONE;
+    if (e_lo <= e_hi && e_lo < C && e_hi >= 0) {
+      any = true;
+#pragma unroll
+      for (int e = 0; e < C; ++e, z += zstep) {
+        u64 val = KEY_NONE;
+        if (e >= e_lo && e <= e_hi) val = mix64(z);
+        v[e] = val;
+        agg = tmin(agg, val);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < C; ++e) v[e] = KEY_NONE;
+    }
+    // chunk minima combined within each k-block (k / C consecutive chunks)
+    const u32 m = k / C;
+    const u64 es = lw_seg_scan_excl<true>(agg, m, sbuf, wv, wf);
+    const u64 ep = lw_seg_scan_excl<false>(agg, m, sbuf, wv, wf);
+    u64 run = es;
+#pragma unroll
+    for (int e = C - 1; e >= 0; --e) {
+      run = tmin(run, v[e]);
+      Qs[e][tid] = run;  // suffix minimum within the k-block
+    }
+    run = ep;
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      run = tmin(run, v[e]);
+      v[e] = run;  // prefix minimum within the k-block
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < C; ++e) v[e] = KEY_NONE;
+  }
+  cl.sync();  // suffix minima of every span of the line are in shared memory
+  if (!(own_dead && prev_dead)) {
+    const u64* Qp = rp == r ? &Qs[0][0] : cl.map_shared_rank(&Qs[0][0], rp);
+    // cell q0 + e reads the suffix minimum at q0 + e - k + 1, element
+    // (e + 1) % C of chunk tid - k/C + (e + 1) / C (a negative chunk lies in
+    // the previous span); the chunk's last cell closes a k-block iff the
+    // chunk is the block's last
+    const u32 m = k / C;
+    const int cb = (int)tid - (int)m;
+    const bool last_chunk = tid % m == m - 1;
+    u64 last = KEY_NONE;
+    u32 anchor = 0;
+    u32 packed[(C + 1) / 2];
+#pragma unroll
+    for (int e = 0; e < C; ++e) {
+      u64 mv = v[e];
+      if (!(e == C - 1 && last_chunk)) {
+        const int c = cb + (e + 1) / C;
+        const int el = (e + 1) % C;
+        u64 qv = KEY_NONE;
+        if (c >= 0) {
+          if (!own_dead) qv = Qs[el][c];
+        } else if (!prev_dead) {
+          qv = Qp[el * LW_THREADS + (c + (int)LW_THREADS)];
+        }
+        mv = tmin(mv, qv);
+      }
+      u32 code = CODE_NONE;
+      if (mv != KEY_NONE) {
+        if (mv != last) {
+          // the winning candidate, from its priority
+          const u32 idx = (u32)((mix64_inverse(mv) - zb) * SM_GAMMA_INV);
+          anchor = F == 0 ? idx - line * L : (idx - (u32)g.LL - line) / L;
+          last = mv;
+        }
+        const u32 x = x0 + q0 + e;
+        code = x >= anchor ? x - anchor : x + L - anchor;
+      }
+      if (e & 1) packed[e >> 1] |= code << 16;
+      else packed[e >> 1] = code;
+    }
+    u16* dst = cout + ((size_t)s * L + line) * L + x0 + q0;
+    if constexpr (C >= 8) {
+#pragma unroll
+      for (int i = 0; i < C / 8; ++i)
+        reinterpret_cast<uint4*>(dst)[i] =
+            make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+    } else if constexpr (C == 4) {
+      *reinterpret_cast<uint2*>(dst) = make_uint2(packed[0], packed[1]);
+    } else if constexpr (C == 2) {
+      *reinterpret_cast<u32*>(dst) = packed[0];
+    } else {
+      *dst = (u16)packed[0];
+    }
+    if (tid == 0) work_add(g, F, P);
+  }
+  // no CTA leaves while another may still read its shared memory
+  cl.sync();
+  if (!own_dead) {
+    if (__syncthreads_or(any)) {
+      if (tid == 0 && !g.st[s].alive) g.st[s].alive = 1;
+    } else if (tid == 0) {
+      fl[r] |= 1u;
+    }
+  }
+}
+
+// Final 2-byte code of every cell from the two orientations' argmin offsets:
+// d for a horizontal winner, CODE_V | d for a vertical one, CODE_NONE if no
+// live candidate covers the cell; in both layouts.  One warp per strip of
+// 32 columns x 16 rows, all its global loads issued first: lane = column,
+// walking down it (vertical winners' priorities and offsets, kept in shared
+// memory), then lane = (row, half-row), walking along it (horizontal
+// winners, compared with the vertical ones), then the transposed write.  A
+// winner's priority is recomputed only when its anchor changes along the
+// walk.  cdead[s * 2 T^2 + strip] is set once every code of the strip is
+// CODE_NONE (it stays so; later rounds skip the strip).
+constexpr u32 LC_WARPS = 8;
+struct LcombSmem {
+  u64 vk[LC_WARPS][32][17];   // vertical winners' priorities [x][y]
+  u16 vd[LC_WARPS][32][18];   // their offsets [x][y]
+  u16 cs[LC_WARPS][16][34];   // final codes [y][x]
+};
+
+__global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH, const u16* cV,
+                                                         u16* code, u16* codeT, u8* cdead) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  LcombSmem& sm = *reinterpret_cast<LcombSmem*>(smem_raw);
+  const u32 s = blockIdx.y;
+  if (g.st[s].done) return;
+  const u32 L = g.L, T = L / 32, NS = 2 * T * T;  // strips per sample
+  const u32 lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const u32 strip = blockIdx.x * LC_WARPS + wp;
+  if (strip >= NS) return;
+  u8* dflag = cdead + (size_t)s * NS + strip;
+  if (*dflag) return;
+  const u32 sy = strip / T, tx = strip - sy * T, Y = sy * 16, X = tx * 32;
+  const u64 zb = g.base[s] + SM_GAMMA;
+  const size_t so = (size_t)s * g.LL;
+  u64 (*vk)[17] = sm.vk[wp];
+  u16 (*vd)[18] = sm.vd[wp];
+  u16 (*cs)[34] = sm.cs[wp];
+  const u32 row = lane & 15, half = lane >> 4;
+  // vertical codes of column X + lane (rows Y .. Y + 15), horizontal codes
+  // of row Y + row (columns X + 16 half ..): 32 bytes each
+  const uint4* vsrc = reinterpret_cast<const uint4*>(cV + so + (size_t)(X + lane) * L + Y);
+  const uint4* hsrc = reinterpret_cast<const uint4*>(cH + so + (size_t)(Y + row) * L + X + 16 * half);
+  const uint4 v0 = __ldg(vsrc), v1 = __ldg(vsrc + 1);
+  const uint4 h0 = __ldg(hsrc), h1 = __ldg(hsrc + 1);
+  const u32 cvw[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+  const u32 chw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+  {
+    const u32 x = X + lane;
+    u32 ca = NONE32;
+    u64 ck = KEY_NONE;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const u32 d = (cvw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+      u64 key = KEY_NONE;
+      if (d != CODE_NONE) {
+        u32 ya = Y + i + L - d;
+        if (ya >= L) ya -= L;
+        if (ya != ca) {
+          ck = mix64(zb + SM_GAMMA * (g.LL + (u64)ya * L + x));
+          ca = ya;
+        }
+        key = ck;
+      }
+      vk[lane][i] = key;
+      vd[lane][i] = (u16)d;
+    }
+  }
+  __syncwarp();
+  bool any = false;
+  {
+    const u32 y = Y + row, xb = 16 * half;
+    u32 ca = NONE32;
+    u64 ck = KEY_NONE;
+    u32 out[8];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const u32 d = (chw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
+      u64 kh = KEY_NONE;
+      if (d != CODE_NONE) {
+        u32 xa = X + xb + i + L - d;
+        if (xa >= L) xa -= L;
+        if (xa != ca) {
+          ck = mix64(zb + SM_GAMMA * ((u64)y * L + xa));
+          ca = xa;
+        }
+        kh = ck;
+      }
+      const u64 kv = vk[xb + i][row];
+      u32 cd = CODE_NONE;
+      if (kh < kv) cd = d;
+      else if (kv < kh) cd = CODE_V | vd[xb + i][row];
+      any |= cd != CODE_NONE;
+      cs[row][xb + i] = (u16)cd;
+      if (i & 1) out[i >> 1] |= cd << 16;
+      else out[i >> 1] = cd;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(code + so + (size_t)y * L + X + xb);
+    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+  }
+  __syncwarp();
+  {
+    u32 out[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      out[i] = (u32)cs[2 * i][lane] | ((u32)cs[2 * i + 1][lane] << 16);
+    uint4* dst = reinterpret_cast<uint4*>(codeT + so + (size_t)(X + lane) * L + Y);
+    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+  }
+  if (lane == 0) work_add(g, 3, 512);
+  if (!__any_sync(FULL, any) && lane == 0) *dflag = 1;
+}
+
+}  // namespace rsak

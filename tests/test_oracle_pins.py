@@ -405,3 +405,13 @@ def test_horizontal_wrapping_probability_at_pc():
         wx += x
         wy += y
     assert abs((wx + wy) / (2 * N) - 0.521058290) < 0.06, (wx / N, wy / N)
+
+
+@pytest.mark.parametrize("L,k", [(1, 1), (5, 2), (16, 3), (64, 4), (128, 64), (300, 17)])
+def test_scan_from_seed_equals_scan_of_the_keys(L, k):
+    # the seeded scan forms its (key, idx) pairs from the key function itself;
+    # it must accept exactly what the scan of the materialised keys accepts
+    for seed in (1, 7, 123456789):
+        a1, o1 = oracle.scan(L, k, oracle.keys(L, seed))
+        a2, o2 = oracle.scan_seed(L, k, seed)
+        assert np.array_equal(a1, a2) and np.array_equal(o1, o2)
