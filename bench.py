@@ -42,6 +42,7 @@ WORKLOADS = {
     "L1024_k32_x64": dict(L=1024, k=32, n=64),
     "L8192_k512_x2": dict(L=8192, k=512, n=2),
     "L8192_k512_x8": dict(L=8192, k=512, n=8),
+    "L16384_k4096_x1": dict(L=16384, k=4096, n=1),
 }
 DEFAULT_WORKLOAD = "L32768_k4096_x8"
 METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"

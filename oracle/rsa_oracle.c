@@ -82,16 +82,15 @@ static void orc_cell(uint32_t L, uint32_t idx, uint32_t i, uint32_t *y, uint32_t
     else        { *y = (y0 + i) % L; *x = x0; }
 }
 
-/* Sort the n = 2L^2 (key, idx) pairs and scan them in ascending key order,
- * accepting a candidate iff its k cells are free.  accepted[] receives the
- * accepted idx in scan order.  Returns n_j, or -1 if two keys are equal (the
- * order would be undefined).  Frees p. */
-static int64_t orc_scan_pairs(uint32_t L, uint32_t k, orc_pair *p, uint64_t n,
-                              uint32_t *accepted, uint8_t *occ)
+/* Scan n = 2L^2 (key, idx) pairs already sorted by key, accepting a
+ * candidate iff its k cells are free.  accepted[] receives the accepted idx
+ * in scan order.  Returns n_j, or -1 if two keys are equal (the order would
+ * be undefined). */
+static int64_t orc_scan_sorted(uint32_t L, uint32_t k, const orc_pair *p, uint64_t n,
+                               uint32_t *accepted, uint8_t *occ)
 {
-    qsort(p, n, sizeof(orc_pair), orc_cmp);
     for (uint64_t i = 1; i < n; ++i)
-        if (p[i].key == p[i - 1].key) { free(p); return -1; }
+        if (p[i].key == p[i - 1].key) return -1;
     memset(occ, 0, (size_t)L * L);
     int64_t nj = 0;
     for (uint64_t s = 0; s < n; ++s) {
@@ -107,11 +106,11 @@ static int64_t orc_scan_pairs(uint32_t L, uint32_t k, orc_pair *p, uint64_t n,
         }
         accepted[nj++] = idx;
     }
-    free(p);
     return nj;
 }
 
-/* Scan the 2L^2 candidates of caller-given keys (Sec. II.B). */
+/* Scan the 2L^2 candidates of caller-given keys in ascending key order
+ * (Sec. II.B). */
 int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
                     uint32_t *accepted, uint8_t *occ)
 {
@@ -119,20 +118,39 @@ int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
     orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
     if (!p) return -2;
     for (uint64_t i = 0; i < n; ++i) { p[i].key = keys[i]; p[i].idx = (uint32_t)i; }
-    return orc_scan_pairs(L, k, p, n, accepted, occ);
+    qsort(p, n, sizeof(orc_pair), orc_cmp);
+    int64_t nj = orc_scan_sorted(L, k, p, n, accepted, occ);
+    free(p);
+    return nj;
 }
 
-/* The same scan for the seeded priorities of oracle_keys, with the pairs
- * formed straight from oracle_key: no separate array of 2L^2 keys, so the
- * largest lattices (L = 32768: 34 GB of pairs) fit in host memory. */
+/* The same scan for the seeded priorities of oracle_keys, for the largest
+ * lattices (L = 32768: 2^31 pairs, 34 GB): no separate key array, and the
+ * sort is split by the top 16 bits of the key -- a counting pass, each pair
+ * written straight into its bucket, then each bucket sorted by itself -- so
+ * no temporary as large as the pairs is needed. */
 int64_t oracle_scan_seed(uint32_t L, uint32_t k, uint64_t seed, uint32_t *accepted,
                          uint8_t *occ)
 {
-    uint64_t n = 2ULL * L * L, b = oracle_base(seed);
+    const uint64_t n = 2ULL * L * L, b = oracle_base(seed), NB = 65536;
+    uint64_t *at = (uint64_t *)calloc(NB + 1, sizeof(uint64_t));
     orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
-    if (!p) return -2;
-    for (uint64_t i = 0; i < n; ++i) { p[i].key = oracle_key(b, i); p[i].idx = (uint32_t)i; }
-    return orc_scan_pairs(L, k, p, n, accepted, occ);
+    if (!at || !p) { free(at); free(p); return -2; }
+    for (uint64_t i = 0; i < n; ++i) at[(oracle_key(b, i) >> 48) + 1] += 1;
+    for (uint64_t j = 0; j < NB; ++j) at[j + 1] += at[j];   /* bucket starts */
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t key = oracle_key(b, i);
+        orc_pair *q = &p[at[key >> 48]++];                    /* next slot of its bucket */
+        q->key = key;
+        q->idx = (uint32_t)i;
+    }
+    /* at[j] is now the end of bucket j (the start of bucket j + 1) */
+    for (uint64_t j = 0, lo = 0; j < NB; lo = at[j], ++j)
+        if (at[j] - lo > 1) qsort(p + lo, at[j] - lo, sizeof(orc_pair), orc_cmp);
+    int64_t nj = orc_scan_sorted(L, k, p, n, accepted, occ);
+    free(p);
+    free(at);
+    return nj;
 }
 
 /* ---- union-find with displacement vectors (Sec. II.C, II.D) ------------ */

@@ -25,9 +25,8 @@
 // k-block.  Suffix minima go to shared memory; the window of a cell whose
 // block b-1 lies in the previous span reads them from that CTA's shared
 // memory over the cluster (distributed shared memory), so no priority is
-// computed twice.  The winner's offset comes from inverting its priority
-// (splitmix64 is a bijection), once per change of the window minimum along
-// the chunk.
+// computed twice.  Every minimum carries the line position of its
+// candidate, so the winner's offset is cell - position.
 //
 // A span with no live anchor has no live anchor in any later round: it is
 // flagged and skips hashing and scans; once it and the span before it are
@@ -49,69 +48,71 @@ struct LwinCfg {
   u32 T;   // occupancy words per line, L / 32
 };
 
-// Exclusive segmented scan (min) of one value per thread over the block,
-// in thread order (BWD: descending).  Segments are runs of m consecutive
-// threads starting at multiples of m.  `buf` holds 256 u64 of scratch.
-template <bool BWD>
-__device__ __forceinline__ u64 lw_seg_scan_excl(u64 a, u32 m, u64* buf, u64* wv, u32* wf) {
+constexpr u32 LW_SENT = 0xFFFFu;  // position of "no candidate"
+
+// (key, position) minimum: a = the smaller of a and b with its position.
+// Keys are distinct except KEY_NONE, which always carries LW_SENT.
+__device__ __forceinline__ void kp_min(u64& a, u32& pa, u64 b, u32 pb) {
+  const bool lt = b < a;
+  a = lt ? b : a;
+  pa = lt ? pb : pa;
+}
+
+// Exclusive prefix and suffix (key, position) minima of one value per
+// thread, within segments of m consecutive threads (m a power of two, the
+// chunks of one k-block): sub-warp shuffles of width min(m, 32), then, for
+// segments of several warps, the totals of the other warps of the segment.
+__device__ __forceinline__ void lw_block_scans(u64 a, u32 pa, u32 m, u64& ep, u32& epp, u64& es,
+                                               u32& esp, u64* wtf, u32* wtfp, u64* wtb,
+                                               u32* wtbp) {
   const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // the thread opens a segment in scan order (its first thread)
-  const bool head = BWD ? (tid % m == m - 1) : (tid % m == 0);
-  u64 v = a;
-  bool f = head;
+  const u32 wd = m < 32 ? m : 32, li = lane & (wd - 1);
+  u64 f = a, b = a;
+  u32 fp = pa, bp = pa;
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const u64 o = BWD ? __shfl_down_sync(FULL, v, d) : __shfl_up_sync(FULL, v, d);
-    const bool of = BWD ? __shfl_down_sync(FULL, f, d) : __shfl_up_sync(FULL, f, d);
-    const bool ok = BWD ? lane + d < 32 : (int)lane >= d;
-    if (ok) {
-      if (!f) v = tmin(v, o);
-      f = f || of;
+  for (u32 d = 1; d < 32; d <<= 1) {
+    const u64 of = __shfl_up_sync(FULL, f, d, wd);
+    const u32 ofp = __shfl_up_sync(FULL, fp, d, wd);
+    const u64 ob = __shfl_down_sync(FULL, b, d, wd);
+    const u32 obp = __shfl_down_sync(FULL, bp, d, wd);
+    if (d < wd) {
+      if (li >= d) kp_min(f, fp, of, ofp);
+      if (li + d < wd) kp_min(b, bp, ob, obp);
     }
   }
-  // totals of each warp (its last thread in scan order)
-  if (lane == (BWD ? 0u : 31u)) {
-    wv[warp] = v;
-    wf[warp] = f;
+  // exclusive: the inclusive value of the previous (next) thread
+  u64 xf = __shfl_up_sync(FULL, f, 1, wd), xb = __shfl_down_sync(FULL, b, 1, wd);
+  u32 xfp = __shfl_up_sync(FULL, fp, 1, wd), xbp = __shfl_down_sync(FULL, bp, 1, wd);
+  if (li == 0) { xf = KEY_NONE; xfp = LW_SENT; }
+  if (li == wd - 1) { xb = KEY_NONE; xbp = LW_SENT; }
+  if (m > 32) {
+    if (lane == 31) { wtf[warp] = f; wtfp[warp] = fp; }
+    if (lane == 0) { wtb[warp] = b; wtbp[warp] = bp; }
+    __syncthreads();
+    const u32 ws = m / 32, w0 = warp & ~(ws - 1);
+    for (u32 w2 = w0; w2 < warp; ++w2) kp_min(xf, xfp, wtf[w2], wtfp[w2]);
+    for (u32 w2 = warp + 1; w2 < w0 + ws; ++w2) kp_min(xb, xbp, wtb[w2], wtbp[w2]);
   }
-  __syncthreads();
-  u64 incl = v;
-  if (!f) {
-    // carry from the warps before this one in scan order, up to a head
-    if (BWD) {
-      for (u32 w2 = warp + 1; w2 < LW_THREADS / 32; ++w2) {
-        incl = tmin(incl, wv[w2]);
-        if (wf[w2]) break;
-      }
-    } else {
-      for (int w2 = (int)warp - 1; w2 >= 0; --w2) {
-        incl = tmin(incl, wv[w2]);
-        if (wf[w2]) break;
-      }
-    }
-  }
-  buf[tid] = incl;
-  __syncthreads();
-  u64 ex = KEY_NONE;
-  if (!head) ex = buf[BWD ? tid + 1 : tid - 1];
-  __syncthreads();  // buf and the warp totals are reused by the next scan
-  return ex;
+  ep = xf; epp = xfp;
+  es = xb; esp = xbp;
 }
 
 // F = 0: rows y of occw, offsets to cH[y][.]; F = 1: columns x (rows of the
 // transposed occT), offsets to cV[x][.].  lflag[((s * 2 + F) * L + line) *
 // nc + r] bit 0: span r of the line has no live anchor (stays so).
+// Minima carry the line position of their candidate, so the offset of the
+// winner is cell - position; no priority is inverted.
 template <int F, int C>
 __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const u32* occw,
                                                      const u32* occT, u16* cout, u8* lflag) {
   namespace cg = cooperative_groups;
-  __shared__ u64 Qs[C][LW_THREADS];      // suffix minimum of chunk t, element e at [e][t]
+  __shared__ u64 Qk[C][LW_THREADS];      // suffix minimum at element e of chunk t: [e][t]
+  __shared__ u16 Qp[C][LW_THREADS];      // its candidate's position on the line
   __shared__ u32 w[LW_THREADS + 2];      // staged occupancy words
   __shared__ u32 nw[LW_THREADS + 2];     // first occupied position at / after word i
-  __shared__ u64 sbuf[LW_THREADS];
-  __shared__ u64 wv[LW_THREADS / 32];
-  __shared__ u32 wf[LW_THREADS / 32];
   __shared__ u32 wmin[LW_THREADS / 32];
+  __shared__ u64 wtf[LW_THREADS / 32], wtb[LW_THREADS / 32];
+  __shared__ u32 wtfp[LW_THREADS / 32], wtbp[LW_THREADS / 32];
   cg::cluster_group cl = cg::this_cluster();
   const u32 nc = lc.nc, r = cl.block_rank();
   const u32 line = blockIdx.x / nc, s = blockIdx.y;
@@ -122,10 +123,15 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
   u8* fl = lflag + ((size_t)(s * 2 + F) * L + line) * nc;
   const bool own_dead = (fl[r] & 1u) != 0, prev_dead = (fl[rp] & 1u) != 0;
   const u32 x0 = r * P;
-  const u32 q0 = tid * C;               // first cell of this thread's chunk (relative to x0)
-  const u64 zb = g.base[s] + SM_GAMMA;  // splitmix64 input of candidate idx: zb + gamma idx
+  const u32 q0 = tid * C;   // first cell of this thread's chunk (relative to x0)
+  const u32 xs = x0 + q0;   // its position on the line
+  const u32 m = k / C;      // chunks per k-block
   u64 v[C];
+#pragma unroll
+  for (int e = 0; e < C; ++e) v[e] = KEY_NONE;
   bool any = false;
+  u64 ep = KEY_NONE, es = KEY_NONE;
+  u32 epp = LW_SENT, esp = LW_SENT;
   if (!own_dead) {
     // occupancy words of [x0, x0 + P + k - 1), around the torus
     const u32 nwords = (P + k + 30) / 32;  // <= 256: P, k <= 4096
@@ -134,9 +140,9 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
     if (tid < nwords) {
       u32 wi = x0 / 32 + tid;
       while (wi >= T) wi -= T;
-      const u32 wd = bits[wi];
-      w[tid] = wd;
-      if (wd) fst = tid * 32 + __ffs(wd) - 1;
+      const u32 wdd = bits[wi];
+      w[tid] = wdd;
+      if (wdd) fst = tid * 32 + __ffs(wdd) - 1;
     }
     // nw[i] = min over words j >= i of their first occupied position
     u32 sm = fst;
@@ -156,88 +162,74 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
     // occupied bit) and the first occupied cell after that word is at least
     // k ahead: an interval e_lo <= e <= e_hi of the chunk's offsets
     const u32 wi = q0 >> 5, rb = q0 & 31u;  // C divides 32: one word holds the chunk
-    const u32 wd = w[wi], nxtw = nw[wi + 1];
-    const int e_lo = wd ? (int)(31 - __clz(wd)) - (int)rb + 1 : 0;
+    const u32 wdd = w[wi], nxtw = nw[wi + 1];
+    const int e_lo = wdd ? (int)(31 - __clz(wdd)) - (int)rb + 1 : 0;
     const int e_hi = nxtw == LW_INF ? C : (int)nxtw - (int)k - (int)q0;
-    const u64 zstep = F == 0 ? SM_GAMMA : SM_GAMMA * (u64)L;
-    u64 z = zb + SM_GAMMA * (F == 0 ? (u64)line * L + x0 + q0
-                                    : g.LL + (u64)(x0 + q0) * L + line);
     u64 agg = KEY_NONE;
+    u32 aggp = LW_SENT;
     if (e_lo <= e_hi && e_lo < C && e_hi >= 0) {
       any = true;
+      const u64 zstep = F == 0 ? SM_GAMMA : SM_GAMMA * (u64)L;
+      u64 z = g.base[s] + SM_GAMMA +
+              SM_GAMMA * (F == 0 ? (u64)line * L + xs : g.LL + (u64)xs * L + line);
 #pragma unroll
       for (int e = 0; e < C; ++e, z += zstep) {
-        u64 val = KEY_NONE;
-        if (e >= e_lo && e <= e_hi) val = mix64(z);
-        v[e] = val;
-        agg = tmin(agg, val);
+        const u64 h = mix64(z);
+        v[e] = (e >= e_lo && e <= e_hi) ? h : KEY_NONE;
+        kp_min(agg, aggp, v[e], xs + e);
       }
-    } else {
-#pragma unroll
-      for (int e = 0; e < C; ++e) v[e] = KEY_NONE;
     }
-    // chunk minima combined within each k-block (k / C consecutive chunks)
-    const u32 m = k / C;
-    const u64 es = lw_seg_scan_excl<true>(agg, m, sbuf, wv, wf);
-    const u64 ep = lw_seg_scan_excl<false>(agg, m, sbuf, wv, wf);
-    u64 run = es;
+    // chunk minima combined within each k-block (m consecutive chunks)
+    lw_block_scans(agg, aggp, m, ep, epp, es, esp, wtf, wtfp, wtb, wtbp);
+  }
+  // suffix minima within the k-block into shared memory (a span without
+  // live anchors publishes "none", so readers need not know)
+  {
+    u64 rk = es;
+    u32 rq = esp;
 #pragma unroll
     for (int e = C - 1; e >= 0; --e) {
-      run = tmin(run, v[e]);
-      Qs[e][tid] = run;  // suffix minimum within the k-block
+      kp_min(rk, rq, v[e], xs + e);
+      Qk[e][tid] = rk;
+      Qp[e][tid] = (u16)rq;
     }
-    run = ep;
-#pragma unroll
-    for (int e = 0; e < C; ++e) {
-      run = tmin(run, v[e]);
-      v[e] = run;  // prefix minimum within the k-block
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < C; ++e) v[e] = KEY_NONE;
   }
   cl.sync();  // suffix minima of every span of the line are in shared memory
   if (!(own_dead && prev_dead)) {
-    const u64* Qp = rp == r ? &Qs[0][0] : cl.map_shared_rank(&Qs[0][0], rp);
-    // cell q0 + e reads the suffix minimum at q0 + e - k + 1, element
-    // (e + 1) % C of chunk tid - k/C + (e + 1) / C (a negative chunk lies in
-    // the previous span); the chunk's last cell closes a k-block iff the
-    // chunk is the block's last
-    const u32 m = k / C;
+    // cell q0 + e needs the suffix minimum at q0 + e - k + 1: element
+    // (e + 1) % C of chunk tid - m + (e + 1) / C, in the previous span when
+    // that chunk index is negative
     const int cb = (int)tid - (int)m;
-    const bool last_chunk = tid % m == m - 1;
-    u64 last = KEY_NONE;
-    u32 anchor = 0;
+    const u64* QkR = rp == r ? &Qk[0][0] : cl.map_shared_rank(&Qk[0][0], rp);
+    const u16* QpR = rp == r ? &Qp[0][0] : cl.map_shared_rank(&Qp[0][0], rp);
+    const int ca = cb, cc = cb + 1;
+    const u64* ka = ca >= 0 ? &Qk[0][ca] : QkR + (ca + (int)LW_THREADS);
+    const u16* pa = ca >= 0 ? &Qp[0][ca] : QpR + (ca + (int)LW_THREADS);
+    const u64* kc = cc >= 0 ? &Qk[0][cc] : QkR + (cc + (int)LW_THREADS);
+    const u16* pc = cc >= 0 ? &Qp[0][cc] : QpR + (cc + (int)LW_THREADS);
+    const bool closes = tid % m == m - 1;  // the chunk's last cell ends its k-block
+    u64 rk = ep;
+    u32 rq = epp;
     u32 packed[(C + 1) / 2];
 #pragma unroll
     for (int e = 0; e < C; ++e) {
-      u64 mv = v[e];
-      if (!(e == C - 1 && last_chunk)) {
-        const int c = cb + (e + 1) / C;
-        const int el = (e + 1) % C;
-        u64 qv = KEY_NONE;
-        if (c >= 0) {
-          if (!own_dead) qv = Qs[el][c];
-        } else if (!prev_dead) {
-          qv = Qp[el * LW_THREADS + (c + (int)LW_THREADS)];
-        }
-        mv = tmin(mv, qv);
+      kp_min(rk, rq, v[e], xs + e);  // prefix minimum within the k-block
+      u64 mk = rk;
+      u32 mq = rq;
+      const int el = (e + 1) % C;
+      if (e < C - 1) {
+        kp_min(mk, mq, ka[el * LW_THREADS], pa[el * LW_THREADS]);
+      } else if (!closes) {
+        kp_min(mk, mq, kc[0], pc[0]);
       }
-      u32 code = CODE_NONE;
-      if (mv != KEY_NONE) {
-        if (mv != last) {
-          // the winning candidate, from its priority
-          const u32 idx = (u32)((mix64_inverse(mv) - zb) * SM_GAMMA_INV);
-          anchor = F == 0 ? idx - line * L : (idx - (u32)g.LL - line) / L;
-          last = mv;
-        }
-        const u32 x = x0 + q0 + e;
-        code = x >= anchor ? x - anchor : x + L - anchor;
-      }
+      const u32 x = xs + e;
+      u32 d = x - mq;
+      if (x < mq) d += L;
+      const u32 code = mq == LW_SENT ? (u32)CODE_NONE : d;
       if (e & 1) packed[e >> 1] |= code << 16;
       else packed[e >> 1] = code;
     }
-    u16* dst = cout + ((size_t)s * L + line) * L + x0 + q0;
+    u16* dst = cout + ((size_t)s * L + line) * L + xs;
     if constexpr (C >= 8) {
 #pragma unroll
       for (int i = 0; i < C / 8; ++i)
@@ -314,17 +306,15 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const u32 d = (cvw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
-      u64 key = KEY_NONE;
-      if (d != CODE_NONE) {
-        u32 ya = Y + i + L - d;
-        if (ya >= L) ya -= L;
-        if (ya != ca) {
-          ck = mix64(zb + SM_GAMMA * (g.LL + (u64)ya * L + x));
-          ca = ya;
-        }
-        key = ck;
+      const bool has = d != CODE_NONE;
+      u32 ya = Y + i + L - d;
+      if (ya >= L) ya -= L;
+      // the only branch: a new anchor along the column
+      if (has && ya != ca) {
+        ck = mix64(zb + SM_GAMMA * (g.LL + (u64)ya * L + x));
+        ca = ya;
       }
-      vk[lane][i] = key;
+      vk[lane][i] = has ? ck : KEY_NONE;
       vd[lane][i] = (u16)d;
     }
   }
@@ -338,20 +328,17 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const u32 d = (chw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
-      u64 kh = KEY_NONE;
-      if (d != CODE_NONE) {
-        u32 xa = X + xb + i + L - d;
-        if (xa >= L) xa -= L;
-        if (xa != ca) {
-          ck = mix64(zb + SM_GAMMA * ((u64)y * L + xa));
-          ca = xa;
-        }
-        kh = ck;
+      const bool has = d != CODE_NONE;
+      u32 xa = X + xb + i + L - d;
+      if (xa >= L) xa -= L;
+      if (has && xa != ca) {
+        ck = mix64(zb + SM_GAMMA * ((u64)y * L + xa));
+        ca = xa;
       }
+      const u64 kh = has ? ck : KEY_NONE;
       const u64 kv = vk[xb + i][row];
-      u32 cd = CODE_NONE;
-      if (kh < kv) cd = d;
-      else if (kv < kh) cd = CODE_V | vd[xb + i][row];
+      const u32 dv = CODE_V | vd[xb + i][row];
+      const u32 cd = kh < kv ? d : (kv < kh ? dv : (u32)CODE_NONE);
       any |= cd != CODE_NONE;
       cs[row][xb + i] = (u16)cd;
       if (i & 1) out[i >> 1] |= cd << 16;
