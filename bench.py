@@ -76,6 +76,8 @@ KERNEL_STEPS = {
     "k_lwin_h": (("rowmin",), 16.0),
     "k_lwin_v": (("colmin",), 16.0),
     "k_lcomb": (("colmin",), 8.0),
+    "k_lacc_h": (("accept", "kill"), 16.5),
+    "k_lacc_v": (("accept", "kill"), 16.5),
     # general path
     "k_row_cmin": (("rowmin",), 16.0),
     "k_col_cmin": (("colmin",), 24.0),
@@ -91,7 +93,8 @@ WORK_CELLS = {"k_tile_cmin": (0, 1.0), "k_tile_accept": (2, 1.0),
               "k_line_cmin_h": (0, 1.0), "k_line_cmin_v": (1, 1.0),
               "k_line_codes": (3, 1.0), "k_line_combine": (3, 1.0),
               "k_line_accept_h": (2, 0.5), "k_line_accept_v": (2, 0.5),
-              "k_lwin_h": (0, 1.0), "k_lwin_v": (1, 1.0), "k_lcomb": (3, 1.0)}
+              "k_lwin_h": (0, 1.0), "k_lwin_v": (1, 1.0), "k_lcomb": (3, 1.0),
+              "k_lacc_h": (2, 0.5), "k_lacc_v": (2, 0.5)}
 # A second view of the tile kernels, which are bound by integer issue:
 # algorithmic 32-bit lane operations (a 64-bit minimum is 4 ops plus 1 when
 # the argmin is tracked, a window minimum is 3 minima per cell, a liveness
@@ -109,6 +112,7 @@ KERNEL_FILE = {"k_tile_cmin": "rsa_tile.cuh", "k_tile_accept": "rsa_tile.cuh",
                "k_line_codes": "rsa_line.cuh", "k_line_accept_h": "rsa_line.cuh",
                "k_line_accept_v": "rsa_line.cuh", "k_lwin_h": "rsa_lwin.cuh",
                "k_lwin_v": "rsa_lwin.cuh", "k_lcomb": "rsa_lwin.cuh",
+               "k_lacc_h": "rsa_lwin.cuh", "k_lacc_v": "rsa_lwin.cuh",
                "k_row_cmin": "rsa_kernels.cuh",
                "k_col_cmin": "rsa_kernels.cuh", "k_row_accept": "rsa_kernels.cuh",
                "k_col_accept": "rsa_kernels.cuh"}

@@ -50,7 +50,7 @@ constexpr size_t SMEM_BUDGET = 160 * 1024;
 size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 struct Layout {
-  size_t occ, occw, occT, cB, code16, code16T, cH, cV, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
+  size_t occ, occw, occT, cB, code16, code16T, cH, cV, masks, dead, owner, cmin, base, node_key, node_idx, node_pos, uf, edges, edges_b,
       ebkt, nkey_b, nbkt, st, seeds, counters, work, keys,
       scratch, total;
 };
@@ -64,8 +64,6 @@ struct Geometry {
   bool lw;
   LwinCfg lw_cfg;
   u32 lw_C;                     // cells per thread of k_lwin
-  LineCfg lw_acc;               // acceptance over the same spans
-  size_t lw_acc_smem;
   size_t line_smem, line_acc_smem, line_codes_smem;
   TileCfg tc;                   // (items filled per run)
   RowCfg row;
@@ -119,12 +117,6 @@ Geometry plan(u32 L, u32 k) {
       G.lw_cfg.nc = L / P;
       G.lw_cfg.T = L / 32;
       G.lw_C = C;
-      G.lw_acc.S = P;
-      G.lw_acc.nseg = L / P;
-      G.lw_acc.nmax = P + k - 1;
-      G.lw_acc.T = L / 32;
-      G.lw_acc.compact = 0;
-      G.lw_acc_smem = line_codes_smem_bytes(G.lw_acc.nmax);
     }
   }
   // ---- row pass: one warp per (row, segment) ----
@@ -200,10 +192,12 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   l.occw = take(bits ? n * LL / 8 : 0);
   l.occT = take(G.line ? n * LL / 8 : 0);
   l.cB = take(lold ? n * LL * 8 : 0);
-  l.code16 = take(G.line ? n * LL * 2 : 0);
-  l.code16T = take(G.line ? n * LL * 2 : 0);
+  l.code16 = take(lold ? n * LL * 2 : 0);
+  l.code16T = take(lold ? n * LL * 2 : 0);
   l.cH = take(lw ? n * LL * 2 : 0);
   l.cV = take(lw ? n * LL * 2 : 0);
+  // acceptance masks: win / first / last, rows then the transposed layout
+  l.masks = take(lw ? 6 * (n * LL / 8) : 0);
   // dead flags: per 32 x 32 tile (tile path); per line segment (or span) of
   // each orientation, then per 32 x 32 code tile (long-k path)
   // (32 x 16 code strips on the argmin-offset path)
@@ -247,14 +241,14 @@ int set_smem(F* fn, size_t bytes) {
 enum Kind {
   KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
   KD_LINE_CMIN_H, KD_LINE_CMIN_V, KD_LINE_COMBINE, KD_LINE_ACCEPT_H, KD_LINE_ACCEPT_V,
-  KD_LINE_CODES, KD_LWIN_H, KD_LWIN_V, KD_LCOMB,
+  KD_LINE_CODES, KD_LWIN_H, KD_LWIN_V, KD_LCOMB, KD_LACC_H, KD_LACC_V,
   KD_ROUND_END, KD_EDGES, KD_BUCKET, KD_SEARCH_INIT, KD_PROBE_COPY, KD_PROBE, KD_DECIDE, KD_COUNT
 };
 const char* const kKindNames[KD_COUNT] = {
     "k_init",         "k_row_cmin",    "k_col_cmin",   "k_row_accept", "k_col_accept",
     "k_tile_cmin",    "k_tile_accept", "k_line_cmin_h", "k_line_cmin_v", "k_line_combine",
     "k_line_accept_h", "k_line_accept_v", "k_line_codes", "k_lwin_h", "k_lwin_v", "k_lcomb",
-    "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
+    "k_lacc_h",       "k_lacc_v",      "k_round_end",  "k_edges",      "k_bucket",     "k_search_init",
     "k_probe_copy",   "k_probe",       "k_search_decide"};
 
 // Optional per-kernel timing with CUDA events recorded around each launch
@@ -610,9 +604,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
     if ((rc = set_smem(k_line_cmin<1>, G.line_smem))) return rc;
     if ((rc = set_smem(k_line_accept<0>, G.line_acc_smem))) return rc;
     if ((rc = set_smem(k_line_accept<1>, G.line_acc_smem))) return rc;
-    const size_t acc_smem = use_lw ? std::max(G.lw_acc_smem, G.line_codes_smem) : G.line_codes_smem;
-    if ((rc = set_smem(k_line_accept_codes<0>, acc_smem))) return rc;
-    if ((rc = set_smem(k_line_accept_codes<1>, acc_smem))) return rc;
+    if ((rc = set_smem(k_line_accept_codes<0>, G.line_codes_smem))) return rc;
+    if ((rc = set_smem(k_line_accept_codes<1>, G.line_codes_smem))) return rc;
     if ((rc = set_smem(k_lcomb, sizeof(LcombSmem)))) return rc;
   } else if (!G.tile) {
     if ((rc = set_smem(k_row<0>, G.row_smem))) return rc;
@@ -650,19 +643,18 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
         u8* cdead = dead + (size_t)n * 2 * h->L * line_nseg;       // [n][T^2]
         u16* cH = reinterpret_cast<u16*>(b + l.cH);
         u16* cV = reinterpret_cast<u16*>(b + l.cV);
-        u16* c16 = reinterpret_cast<u16*>(b + l.code16);
-        u16* c16T = reinterpret_cast<u16*>(b + l.code16T);
+        u32* mk = reinterpret_cast<u32*>(b + l.masks);
+        const size_t mw = (size_t)n * LL / 32;  // words of one mask array
+        const AccMasks mh{mk, mk + mw, mk + 2 * mw}, mv{mk + 3 * mw, mk + 4 * mw, mk + 5 * mw};
         if (launch_lwin<0>(h, g, G, occw, occT, cH, lflag, n, st) != cudaSuccess) body_rc = RSA_ECUDA;
         if (launch_lwin<1>(h, g, G, occw, occT, cV, lflag, n, st) != cudaSuccess) body_rc = RSA_ECUDA;
         launch(h, KD_LCOMB, k_lcomb, dim3((2 * G.tc.T2 + LC_WARPS - 1) / LC_WARPS, n),
-               dim3(LC_WARPS * 32), sizeof(LcombSmem), st, g, (const u16*)cH, (const u16*)cV, c16,
-               c16T, cdead);
+               dim3(LC_WARPS * 32), sizeof(LcombSmem), st, g, (const u16*)cH, (const u16*)cV, mh,
+               mv, cdead);
         const dim3 ag(h->L * line_nseg, n);
-        launch(h, KD_LINE_ACCEPT_H, k_line_accept_codes<0>, ag, dim3(LINE_THREADS),
-               G.lw_acc_smem, st, g, G.lw_acc, occw, occT, (const u16*)c16, (const u16*)c16T,
+        launch(h, KD_LACC_H, k_lacc<0>, ag, dim3(LW_THREADS), 0, st, g, G.lw_cfg, occw, occT, mh,
                (const u8*)lflag);
-        launch(h, KD_LINE_ACCEPT_V, k_line_accept_codes<1>, ag, dim3(LINE_THREADS),
-               G.lw_acc_smem, st, g, G.lw_acc, occw, occT, (const u16*)c16, (const u16*)c16T,
+        launch(h, KD_LACC_V, k_lacc<1>, ag, dim3(LW_THREADS), 0, st, g, G.lw_cfg, occw, occT, mv,
                (const u8*)lflag);
       } else if (G.line) {
         const dim3 lg(h->L * G.lc.nseg, n), tg(G.tc.T2, n);

@@ -8,9 +8,12 @@
 //   k_lwin<1>   the same along each column (rows of the transposed
 //               occupancy), stored transposed;
 //   k_lcomb     per cell, the smaller of the two winners' priorities (both
-//               recomputed from their anchors) picks the final 2-byte code,
-//               written in both layouts (32 x 16 strips, one warp each);
-//   k_line_accept_codes<F>  acceptance from code runs (rsa_line.cuh).
+//               recomputed from their anchors) picks the final winner, kept
+//               as bit masks in its orientation's layout (32 x 16 strips, one
+//               warp each);
+//   k_lacc<F>   acceptance along lines from the masks, 32 anchors per word
+//               operation, and the accepted k-mers' nodes, occupancy and
+//               owners.
 //
 // k_lwin is van Herk / Gil-Werman with blocks of k cells aligned on the line
 // (L is a multiple of k, so the blocks tile the torus): the window of cell x
@@ -255,30 +258,44 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
   }
 }
 
-// Final 2-byte code of every cell from the two orientations' argmin offsets:
-// d for a horizontal winner, CODE_V | d for a vertical one, CODE_NONE if no
-// live candidate covers the cell; in both layouts.  One warp per strip of
+// Acceptance masks of one orientation: one bit per cell, 32 cells per word
+// along that orientation's own lines (rows for horizontal candidates, the
+// transposed layout for vertical ones).
+struct AccMasks {
+  u32* win;    // the cell's final winner has this orientation
+  u32* first;  // ... and the cell is its winner's first cell (offset 0)
+  u32* last;   // ... and the cell is its winner's last cell (offset k - 1)
+};
+
+// Final winner of every cell from the two orientations' argmin offsets: the
+// candidate of smaller priority (both recomputed from their anchors), kept
+// as the acceptance masks of its orientation.  A candidate anchored at a is
+// accepted iff it is the smallest live candidate on each of its k cells, and
+// since the winners' anchors are monotone along a line that holds iff cell
+// a has it as winner at offset 0, cell a + k - 1 at offset k - 1, and every
+// cell in between is won by its orientation (k_lacc).  One warp per strip of
 // 32 columns x 16 rows, all its global loads issued first: lane = column,
 // walking down it (vertical winners' priorities and offsets, kept in shared
 // memory), then lane = (row, half-row), walking along it (horizontal
-// winners, compared with the vertical ones), then the transposed write.  A
-// winner's priority is recomputed only when its anchor changes along the
-// walk.  cdead[s * 2 T^2 + strip] is set once every code of the strip is
-// CODE_NONE (it stays so; later rounds skip the strip).
+// winners, compared with the vertical ones; row masks), then lane = column
+// again for the column masks.  A winner's priority is recomputed only when
+// its anchor changes along the walk.  cdead[s * 2 T^2 + strip] is set once
+// no cell of the strip is covered by a live candidate (it stays so, with
+// its masks zero; later rounds skip it).
 constexpr u32 LC_WARPS = 8;
 struct LcombSmem {
   u64 vk[LC_WARPS][32][17];   // vertical winners' priorities [x][y]
   u16 vd[LC_WARPS][32][18];   // their offsets [x][y]
-  u16 cs[LC_WARPS][16][34];   // final codes [y][x]
+  u16 cs[LC_WARPS][16][34];   // final codes [y][x]: d, CODE_V | d or CODE_NONE
 };
 
 __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH, const u16* cV,
-                                                         u16* code, u16* codeT, u8* cdead) {
+                                                         AccMasks mh, AccMasks mv, u8* cdead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LcombSmem& sm = *reinterpret_cast<LcombSmem*>(smem_raw);
   const u32 s = blockIdx.y;
   if (g.st[s].done) return;
-  const u32 L = g.L, T = L / 32, NS = 2 * T * T;  // strips per sample
+  const u32 L = g.L, k = g.k, T = L / 32, NS = 2 * T * T;  // strips per sample
   const u32 lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const u32 strip = blockIdx.x * LC_WARPS + wp;
   if (strip >= NS) return;
@@ -291,8 +308,8 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
   u16 (*vd)[18] = sm.vd[wp];
   u16 (*cs)[34] = sm.cs[wp];
   const u32 row = lane & 15, half = lane >> 4;
-  // vertical codes of column X + lane (rows Y .. Y + 15), horizontal codes
-  // of row Y + row (columns X + 16 half ..): 32 bytes each
+  // vertical offsets of column X + lane (rows Y .. Y + 15), horizontal
+  // offsets of row Y + row (columns X + 16 half ..): 32 bytes each
   const uint4* vsrc = reinterpret_cast<const uint4*>(cV + so + (size_t)(X + lane) * L + Y);
   const uint4* hsrc = reinterpret_cast<const uint4*>(cH + so + (size_t)(Y + row) * L + X + 16 * half);
   const uint4 v0 = __ldg(vsrc), v1 = __ldg(vsrc + 1);
@@ -324,7 +341,7 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
     const u32 y = Y + row, xb = 16 * half;
     u32 ca = NONE32;
     u64 ck = KEY_NONE;
-    u32 out[8];
+    u32 bw = 0, b0 = 0, bk = 0;  // row mask bits of this half-row
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const u32 d = (chw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
@@ -338,28 +355,177 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
       const u64 kh = has ? ck : KEY_NONE;
       const u64 kv = vk[xb + i][row];
       const u32 dv = CODE_V | vd[xb + i][row];
-      const u32 cd = kh < kv ? d : (kv < kh ? dv : (u32)CODE_NONE);
+      const bool hw = kh < kv;
+      const u32 cd = hw ? d : (kv < kh ? dv : (u32)CODE_NONE);
       any |= cd != CODE_NONE;
       cs[row][xb + i] = (u16)cd;
-      if (i & 1) out[i >> 1] |= cd << 16;
-      else out[i >> 1] = cd;
+      bw |= (u32)hw << i;
+      b0 |= (u32)(hw && d == 0) << i;
+      bk |= (u32)(hw && d == k - 1) << i;
     }
-    uint4* dst = reinterpret_cast<uint4*>(code + so + (size_t)y * L + X + xb);
-    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    // the two halves of a row make one mask word
+    bw |= __shfl_down_sync(FULL, bw, 16) << 16;
+    b0 |= __shfl_down_sync(FULL, b0, 16) << 16;
+    bk |= __shfl_down_sync(FULL, bk, 16) << 16;
+    if (half == 0) {
+      const size_t wi = ((size_t)s * L + y) * T + tx;
+      mh.win[wi] = bw;
+      mh.first[wi] = b0;
+      mh.last[wi] = bk;
+    }
   }
   __syncwarp();
   {
-    u32 out[8];
+    // column masks: bits Y .. Y + 15 of column X + lane, half a word of
+    // the transposed layout
+    u32 bw = 0, b0 = 0, bk = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      out[i] = (u32)cs[2 * i][lane] | ((u32)cs[2 * i + 1][lane] << 16);
-    uint4* dst = reinterpret_cast<uint4*>(codeT + so + (size_t)(X + lane) * L + Y);
-    dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-    dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    for (int i = 0; i < 16; ++i) {
+      const u32 cd = cs[i][lane];
+      const bool vw = cd != CODE_NONE && (cd & CODE_V);
+      const u32 dv = cd & ~(u32)CODE_V;
+      bw |= (u32)vw << i;
+      b0 |= (u32)(vw && dv == 0) << i;
+      bk |= (u32)(vw && dv == k - 1) << i;
+    }
+    const size_t hi = (((size_t)s * L + X + lane) * T + (Y >> 5)) * 2 + ((Y >> 4) & 1);
+    reinterpret_cast<u16*>(mv.win)[hi] = (u16)bw;
+    reinterpret_cast<u16*>(mv.first)[hi] = (u16)b0;
+    reinterpret_cast<u16*>(mv.last)[hi] = (u16)bk;
   }
   if (lane == 0) work_add(g, 3, 512);
   if (!__any_sync(FULL, any) && lane == 0) *dflag = 1;
+}
+
+// Record accepted candidate `idx` (anchor at position `pos` of line `line`,
+// orientation F) with one warp: its node (key, idx, packed anchor), its k
+// cells in the occupancy bits of both layouts, their owner ids.
+template <int F>
+__device__ void lacc_record(const Group& g, u32 s, u32 line, u32 pos, u32* occw, u32* occT,
+                            u32 T) {
+  const u32 lane = threadIdx.x & 31, L = g.L, k = g.k;
+  SampleState& st = g.st[s];
+  const u32 y0 = F == 0 ? line : pos, x0 = F == 0 ? pos : line;
+  const u32 idx = (u32)((u64)F * g.LL + (u64)y0 * L + x0);
+  u32 node = 0;
+  if (lane == 0) {
+    node = atomicAdd(&st.n_nodes, 1u);
+    if (node < g.cap_nodes) {
+      const size_t nb = (size_t)s * g.cap_nodes + node;
+      g.node_key[nb] = mix64(g.base[s] + SM_GAMMA * ((u64)idx + 1));
+      g.node_idx[nb] = idx;
+      g.node_pos[nb] = ((u32)F << 31) | (y0 << 15) | x0;
+    } else {
+      atomicOr(&st.status, ST_NODE_OVF);
+    }
+  }
+  node = __shfl_sync(FULL, node, 0);
+  if (node >= g.cap_nodes) return;
+  u32* own_line = (F == 0 ? occw : occT) + ((size_t)s * L + line) * T;  // along the k-mer
+  u32* cross = (F == 0 ? occT : occw) + (size_t)s * L * T;              // across it
+  u32* own = g.owner + (size_t)s * g.LL;
+  // the k-mer's cells pos .. pos + k - 1 (around the torus): whole and
+  // partial words of its own line
+  for (u32 j = lane; j * 32 < k + 32; j += 32) {
+    const u32 c0 = pos + 32 * j;  // first cell of this piece (unwrapped)
+    if (32 * j >= k) break;
+    const u32 n = min(32u, k - 32 * j);
+    u32 c = c0 >= L ? c0 - L : c0;
+    // up to two words: the cells c .. c + n - 1 starting at bit c & 31
+    const u32 b = c & 31u, wi = c >> 5;
+    const u64 bits = (n == 32 ? 0xFFFFFFFFull : ((1ull << n) - 1ull)) << b;
+    atomicOr(own_line + wi, (u32)bits);
+    if (bits >> 32) atomicOr(own_line + (wi + 1 == T ? 0 : wi + 1), (u32)(bits >> 32));
+  }
+  for (u32 i = lane; i < k; i += 32) {
+    u32 c = pos + i;
+    if (c >= L) c -= L;
+    // the cell is (line, c) along the k-mer: bit `line` of word c's column
+    atomicOr(cross + (size_t)c * T + (line >> 5), 1u << (line & 31u));
+    if (F == 0) own[(size_t)line * L + c] = node;
+    else own[(size_t)c * L + line] = node | OWN_V;
+  }
+}
+
+// Acceptance along lines from the masks of k_lcomb (F = 0: rows, horizontal
+// candidates; F = 1: columns, vertical ones).  One CTA per span of P
+// anchors (skipped when k_lwin found no live anchor there).  For the 32
+// anchors of a word: "won from its first cell" is the first-mask word,
+// "won at its last cell" the last-mask shifted by k - 1 cells, and "every
+// cell won by this orientation" holds for the anchors a in an interval: past
+// the word's last unwon cell and at least k before the next unwon cell
+// after the word.  The accepted candidates (disjoint along the line, at
+// most P / k + 1) are recorded one per warp.
+template <int F>
+__global__ void __launch_bounds__(LW_THREADS) k_lacc(Group g, LwinCfg lc, u32* occw, u32* occT,
+                                                     AccMasks am, const u8* lflag) {
+  __shared__ u32 mw[3][LW_THREADS + 2];  // win, first, last words from x0
+  __shared__ u32 nz[LW_THREADS + 2];     // first unwon cell at / after word i
+  __shared__ u32 wmin[LW_THREADS / 32];
+  __shared__ u32 acc[LINE_ACC];
+  __shared__ u32 nacc;
+  const u32 s = blockIdx.y;
+  if (g.st[s].done) return;
+  const u32 L = g.L, k = g.k, T = lc.T, P = lc.P, nc = lc.nc;
+  const u32 line = blockIdx.x / nc, r = blockIdx.x - line * nc;
+  if (lflag[((size_t)(s * 2 + F) * L + line) * nc + r] & 1u) return;
+  const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 x0 = r * P;
+  // words of [x0, x0 + P + k + 32): the last-mask shift reads one word past
+  // the last cell of the last anchor
+  const u32 nwords = (P + k) / 32 + 1;  // <= 257
+  const size_t lb = ((size_t)s * L + line) * T;
+  for (u32 i = tid; i < nwords; i += LW_THREADS) {
+    u32 wi = x0 / 32 + i;
+    while (wi >= T) wi -= T;
+    mw[0][i] = am.win[lb + wi];
+    mw[1][i] = am.first[lb + wi];
+    mw[2][i] = am.last[lb + wi];
+  }
+  if (tid == 0) nacc = 0;
+  __syncthreads();
+  // nz[i] = min over words j >= i of their first unwon cell (words past
+  // 255 lie beyond every anchor's last cell)
+  u32 fz = LW_INF;
+  if (tid < nwords && ~mw[0][tid]) fz = tid * 32 + __ffs(~mw[0][tid]) - 1;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const u32 o = __shfl_down_sync(FULL, fz, d);
+    if (lane + d < 32) fz = min(fz, o);
+  }
+  if (lane == 0) wmin[warp] = fz;
+  __syncthreads();
+  for (u32 w2 = warp + 1; w2 < LW_THREADS / 32; ++w2) fz = min(fz, wmin[w2]);
+  nz[tid] = fz;
+  if (tid == 0) nz[LW_THREADS] = LW_INF;
+  __syncthreads();
+  if (tid == 0) work_add(g, 2, P);
+  for (u32 i = tid; i < P / 32; i += LW_THREADS) {
+    const u32 unwon = ~mw[0][i], nxt = nz[i + 1];
+    // anchors 32 i + b with b > (last unwon bit of word i) and
+    // 32 i + b + k <= nxt
+    const int lo = unwon ? (int)(31 - __clz(unwon)) + 1 : 0;
+    const int hi = nxt == LW_INF ? 31 : min(31, (int)nxt - (int)k - (int)(32 * i));
+    u32 run = 0;
+    if (lo <= hi) run = (0xFFFFFFFFu >> (31 - hi)) & (0xFFFFFFFFu << lo);
+    const u32 base = 32 * i + k - 1, wq = base >> 5, sh = base & 31u;
+    const u32 lastw = sh ? (mw[2][wq] >> sh) | (mw[2][wq + 1] << (32 - sh)) : mw[2][wq];
+    u32 acc_bits = run & mw[1][i] & lastw;
+    while (acc_bits) {
+      const u32 b = __ffs(acc_bits) - 1;
+      acc_bits &= acc_bits - 1;
+      const u32 slot = atomicAdd(&nacc, 1u);
+      if (slot < LINE_ACC) acc[slot] = x0 + 32 * i + b;
+    }
+  }
+  __syncthreads();
+  const u32 na = nacc;
+  if (na > LINE_ACC) {
+    if (tid == 0) atomicOr(&g.st[s].status, ST_NODE_OVF);
+    return;
+  }
+  for (u32 j = warp; j < na; j += LW_THREADS / 32)
+    lacc_record<F>(g, s, line, acc[j], occw, occT, T);
 }
 
 }  // namespace rsak
