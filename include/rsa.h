@@ -91,6 +91,62 @@ int rsa_run_keys(rsa_t *h, const uint64_t *keys, void *stream);
 int rsa_run_static(uint32_t L, uint32_t k, const uint64_t *seeds, uint32_t n, uint32_t *n_j,
                    uint32_t *n_c, void *stream);
 
+/* ---- batching of uneven shapes (no counterpart in the paper: a way of
+ * running many of its samples at once) ---------------------------------- */
+
+/* Small lattices, one CTA per sample: all greedy rounds and the whole
+ * first-wrap search of a sample run in one CTA's shared memory, and the n
+ * samples -- of any mix of shapes -- run in one persistent launch (each CTA
+ * takes the next sample from a work counter).  Sample i has lattice L[i],
+ * k-mer length k[i] and seed seeds[i] (host arrays of n, read); n_j, n_c
+ * are host arrays of n (written).  Results equal rsa_run_seeds +
+ * rsa_results for the same (L, k, seed).  Every sample needs L <= 128 and
+ * L^2 / k <= 4096 (RSA_EINVAL otherwise).  threads: CTA size, a multiple of
+ * 32 up to 1024 (0 = 512).  Allocates its job table stream-ordered on
+ * `stream` and synchronises it; returns the first per-sample error code. */
+int rsa_run_small(const uint32_t *L, const uint32_t *k, const uint64_t *seeds, uint32_t n,
+                  uint32_t threads, uint32_t *n_j, uint32_t *n_c, void *stream);
+
+/* A batch of samples of uneven shapes (same arrays as rsa_run_small, any
+ * 1 <= k <= L <= 32768): samples are grouped by shape, each shape runs the
+ * way rsa_tune picks for it, the small-lattice groups together in one
+ * persistent launch and every other shape on its own handle and stream, all
+ * concurrently (one host thread per such shape).  Work queued on `stream`
+ * before the call runs first, work queued after it runs after the batch.
+ * Handles and streams of the shapes seen are kept for later calls (their
+ * device memory too) until rsa_mix_release().  Results are the same as
+ * running each sample alone.  Calls that share a shape run one at a time on
+ * it.  Set RSA_AUTOTUNE=0 to use the default choices instead of timing. */
+int rsa_run_mix(const uint32_t *L, const uint32_t *k, const uint64_t *seeds, uint32_t n,
+                uint32_t *n_j, uint32_t *n_c, void *stream);
+void rsa_mix_release(void);
+
+/* How a shape runs: RSA_MODE_SMALL (one CTA per sample, `threads` per CTA)
+ * or RSA_MODE_GLOBAL (the tiled / long-k / general kernels over the whole
+ * batch, `rounds_per_check` greedy rounds per captured graph chunk and host
+ * check).  ms_per_sample is the time measured when the choice was made. */
+#define RSA_MODE_GLOBAL 0
+#define RSA_MODE_SMALL 1
+typedef struct {
+  uint32_t mode, threads, rounds_per_check;
+  double ms_per_sample;
+} rsa_tune_t;
+
+/* The choice for (L, k) and a batch of n samples on the current GPU.  Looked
+ * up in a per-process table backed by a JSON-lines file ($RSA_TUNE_CACHE,
+ * else $HOME/.cache/rsa_gb300/tune.jsonl), keyed by (GPU name, L, k, n
+ * rounded up to a power of two).  If absent and `measure` is non-zero, every
+ * candidate (small mode at 256 / 512 / 1024 threads where the shape fits it;
+ * the global path at 2 / 4 / 8 rounds per check) is timed once on seeds
+ * 1 .. n (at most 8 GB of workspace) and the fastest is kept and appended
+ * to the file; otherwise a default is returned (small mode at 512 threads
+ * where it fits, else the global path at 4). */
+int rsa_tune(uint32_t L, uint32_t k, uint32_t n, int measure, rsa_tune_t *out);
+
+/* Greedy rounds per captured graph chunk and host check of later runs on
+ * this handle (1 .. 64, default 4).  Results do not depend on it. */
+int rsa_set_rounds_per_check(rsa_t *h, uint32_t rounds);
+
 /* Copy the last run's results to caller-owned host arrays of length n
  * (n <= samples of the last run; either pointer may be NULL).  Synchronises
  * the run's stream.  Returns the first per-sample error code, if any; a

@@ -42,7 +42,7 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 constexpr size_t ALIGN = 256;
-constexpr u32 ROUND_CHECK = 4;   // greedy rounds between host checks
+constexpr u32 ROUND_CHECK = 4;   // greedy rounds between host checks (default)
 constexpr u32 PROBE_CHECK = 4;   // bisection probes between host checks
 constexpr u32 PROBE_CAP = 40;    // rank bisection (<= 31 halvings) plus the initial probe
 constexpr size_t SMEM_BUDGET = 160 * 1024;
@@ -238,6 +238,12 @@ int set_smem(F* fn, size_t bytes) {
 
 }  // namespace
 
+// The thread's error message, set by the other translation units of the
+// library (rsa_mix.cu) as well.
+namespace rsa_detail {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace rsa_detail
+
 enum Kind {
   KD_INIT, KD_ROW_CMIN, KD_COL_CMIN, KD_ROW_ACCEPT, KD_COL_ACCEPT, KD_TILE_CMIN, KD_TILE_ACCEPT,
   KD_LINE_CMIN_H, KD_LINE_CMIN_V, KD_LINE_COMBINE, KD_LINE_ACCEPT_H, KD_LINE_ACCEPT_V,
@@ -291,6 +297,7 @@ struct rsa {
   // chunks the previous run needed before its samples were done: the next
   // run launches that many before its first device->host check
   u32 round_chunks_hint = 1, probe_chunks_hint = 1;
+  u32 round_check = ROUND_CHECK;  // greedy rounds per graph chunk / host check
   // test-only lowered caps of the device loops (0 = default; rsa_test_caps)
   u32 t_round = 0, t_uf = 0, t_probe = 0, t_edges = 0;
   struct GraphSlot {
@@ -298,7 +305,7 @@ struct rsa {
     const void* ws = nullptr;
     u32 n = 0;
     bool keys = false;
-    u32 caps[4] = {0, 0, 0, 0};  // test caps baked into the captured arguments
+    u32 caps[5] = {0, 0, 0, 0, 0};  // test caps and rounds per chunk baked into the graph
     unsigned long long launches[32] = {};
   } g_round, g_probe;
 };
@@ -520,7 +527,7 @@ int run_chunk(rsa_t* h, rsa_t::GraphSlot& gs, cudaStream_t stream, u32 n, B body
     body(stream);
     return launch_check("chunk launches");
   }
-  const u32 caps[4] = {h->t_round, h->t_uf, h->t_probe, h->t_edges};
+  const u32 caps[5] = {h->t_round, h->t_uf, h->t_probe, h->t_edges, h->round_check};
   if (!(gs.exec && gs.ws == h->ws && gs.n == n && gs.keys == h->with_keys &&
         std::memcmp(gs.caps, caps, sizeof(caps)) == 0)) {
     drop_graph(gs);
@@ -634,7 +641,7 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   u64* cB = reinterpret_cast<u64*>(b + l.cB);
   int body_rc = 0;
   auto rounds = [&](cudaStream_t st) {
-    for (u32 i = 0; i < ROUND_CHECK; ++i) {
+    for (u32 i = 0; i < h->round_check; ++i) {
       if (cudaMemsetAsync(d_counter, 0, 4, st) != cudaSuccess) body_rc = RSA_ECUDA;
       if (G.tile) {
         if (launch_tile(h, g, tc, occw, dead, tgrid, st)) body_rc = RSA_EINVAL;
@@ -1076,6 +1083,14 @@ int rsa_test_caps(rsa_t* h, uint32_t round_cap, uint32_t uf_steps, uint32_t prob
   h->t_uf = uf_steps;
   h->t_probe = probe_cap;
   h->t_edges = edge_cap;
+  return 0;
+}
+
+int rsa_set_rounds_per_check(rsa_t* h, uint32_t rounds) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  if (rounds < 1 || rounds > 64) return fail(RSA_EINVAL, "rounds per check must be in 1 .. 64");
+  if (rounds != h->round_check) h->round_chunks_hint = 1;
+  h->round_check = rounds;
   return 0;
 }
 

@@ -127,6 +127,23 @@ __device__ __forceinline__ u64 cand_key(const Group& g, u32 s, u64 idx) {
 }
 
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return b < a ? b : a; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return b > a ? b : a; }
+
+// Shared by the engine and the small-lattice kernel.
+// Position of cell (cy, cx) inside the k-mer whose anchor is packed as
+// o << 31 | y0 << 15 | x0; *o receives the orientation.
+__device__ __forceinline__ u32 pos_in_kmer(u32 pos, u32 cy, u32 cx, u32 L, u32* o) {
+  const u32 oo = pos >> 31, y0 = (pos >> 15) & 0x7FFFu, x0 = pos & 0x7FFFu;
+  *o = oo;
+  const u32 d = oo == 0 ? cx - x0 : cy - y0;
+  return (int)d < 0 ? d + L : d;
+}
+
+__device__ __forceinline__ u64 uf_pack(u32 p, u32 dx, u32 dy) {
+  return (u64)p | ((u64)(dx & 0xFFFFu) << 32) | ((u64)(dy & 0xFFFFu) << 48);
+}
+
+constexpr u32 UF_CAP = 1u << 20;  // default walk / retry cap (Group::uf_cap)
 
 // ---------------------------------------------------------------------
 // Segmented min-scans used by the window minimum.  A window of width k

@@ -221,15 +221,6 @@ __global__ void k_round_end(Group g, u32 round_cap, u32* n_active) {
 // +x) / column 0 (for +y) so that runs that close around the torus are kept.
 // Only edges whose m1 == m2 and delta == 0 (inside one k-mer) are dropped.
 // ---------------------------------------------------------------------
-// Position of cell (cy, cx) inside the k-mer whose anchor is packed as
-// o << 31 | y0 << 15 | x0; *o receives the orientation.
-__device__ __forceinline__ u32 pos_in_kmer(u32 pos, u32 cy, u32 cx, u32 L, u32* o) {
-  const u32 oo = pos >> 31, y0 = (pos >> 15) & 0x7FFFu, x0 = pos & 0x7FFFu;
-  *o = oo;
-  const u32 d = oo == 0 ? cx - x0 : cy - y0;
-  return (int)d < 0 ? d + L : d;
-}
-
 // Lifted displacement of the contact between cell (y, x) of node m1 and its
 // neighbour (by, bx) in direction dir of node m2, packed as 16+16 bits.
 __device__ __forceinline__ u32 contact_delta(const Group& g, u32 s, u32 y, u32 x, u32 by, u32 bx,
@@ -398,11 +389,6 @@ __global__ void __launch_bounds__(1024) k_bucket(Group g) {
 // A wrap is a cycle of primitive winding (a, b) times L; for L < 65536 its
 // offset is never 0 modulo 2^16, so 16-bit offsets decide exactly.
 // ---------------------------------------------------------------------
-__device__ __forceinline__ u64 uf_pack(u32 p, u32 dx, u32 dy) {
-  return (u64)p | ((u64)(dx & 0xFFFFu) << 32) | ((u64)(dy & 0xFFFFu) << 48);
-}
-
-constexpr u32 UF_CAP = 1u << 20;  // default walk / retry cap (Group::uf_cap)
 
 // Root of x and x's offset from it.  Path halving by CAS; a failed CAS is
 // harmless because every stored (parent, offset) pair stays a true ancestor

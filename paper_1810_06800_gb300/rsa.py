@@ -23,10 +23,20 @@ SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_
            "rsa_results",
            "rsa_sample_stats", "rsa_contacts", "rsa_cluster_sizes", "rsa_wrap_dirs", "rsa_accepted",
            "rsa_workspace_bytes", "rsa_bind_workspace", "rsa_test_caps",
-           "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
+           "rsa_run_small", "rsa_run_mix", "rsa_tune", "rsa_set_rounds_per_check",
+           "rsa_mix_release", "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
 _lib = None
+
+
+RSA_MODE_GLOBAL, RSA_MODE_SMALL = 0, 1
+
+
+class TuneT(ctypes.Structure):
+    """rsa_tune_t: how a shape runs (see include/rsa.h)."""
+    _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32),
+                ("rounds_per_check", ctypes.c_uint32), ("ms_per_sample", ctypes.c_double)]
 
 
 class RSAError(RuntimeError):
@@ -63,6 +73,11 @@ def load():
     lib.rsa_workspace_bytes.argtypes = [u32, u32, u32, ctypes.POINTER(u64)]
     lib.rsa_bind_workspace.argtypes = [vp, vp, u64]
     lib.rsa_test_caps.argtypes = [vp, u32, u32, u32, u32]
+    lib.rsa_run_small.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp]
+    lib.rsa_run_mix.argtypes = [vp, vp, vp, u32, vp, vp, vp]
+    lib.rsa_tune.argtypes = [u32, u32, u32, ip, ctypes.POINTER(TuneT)]
+    lib.rsa_set_rounds_per_check.argtypes = [vp, u32]
+    lib.rsa_mix_release.argtypes = []
     lib.rsa_destroy.argtypes = [vp]
     lib.rsa_destroy.restype = None
     lib.rsa_profile.argtypes = [vp, ip]
@@ -74,6 +89,7 @@ def load():
     lib.rsa_last_error.restype = ctypes.c_char_p
     for name in SYMBOLS[:-3]:
         getattr(lib, name).restype = ip
+    lib.rsa_mix_release.restype = None
     _lib = lib
     return lib
 
@@ -126,6 +142,51 @@ def rsa_run_static(L: int, k: int, seeds, stream=None):
     _check(load().rsa_run_static(L, k, a.ctypes.data, a.size, nj.ctypes.data, nc.ctypes.data,
                                  _stream_ptr(stream)))
     return nj, nc
+
+
+def _shape_arrays(L, k, seeds):
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    n = seeds.size
+    Ls = np.ascontiguousarray(np.broadcast_to(np.asarray(L, dtype=np.uint32), (n,)))
+    ks = np.ascontiguousarray(np.broadcast_to(np.asarray(k, dtype=np.uint32), (n,)))
+    return Ls, ks, seeds
+
+
+def rsa_run_small(L, k, seeds, threads: int = 0, stream=None):
+    """Small lattices, one CTA per sample, any mix of shapes in one launch.
+    L and k are scalars or per-sample arrays.  Returns (n_j, n_c)."""
+    Ls, ks, sd = _shape_arrays(L, k, seeds)
+    nj = np.zeros(sd.size, dtype=np.uint32)
+    nc = np.zeros(sd.size, dtype=np.uint32)
+    _check(load().rsa_run_small(Ls.ctypes.data, ks.ctypes.data, sd.ctypes.data, sd.size, threads,
+                                nj.ctypes.data, nc.ctypes.data, _stream_ptr(stream)))
+    return nj, nc
+
+
+def rsa_run_mix(L, k, seeds, stream=None):
+    """A batch of samples of uneven shapes (per-sample L, k, seed arrays),
+    each shape run the way rsa_tune picks.  Returns (n_j, n_c)."""
+    Ls, ks, sd = _shape_arrays(L, k, seeds)
+    nj = np.zeros(sd.size, dtype=np.uint32)
+    nc = np.zeros(sd.size, dtype=np.uint32)
+    _check(load().rsa_run_mix(Ls.ctypes.data, ks.ctypes.data, sd.ctypes.data, sd.size,
+                              nj.ctypes.data, nc.ctypes.data, _stream_ptr(stream)))
+    return nj, nc
+
+
+def rsa_mix_release():
+    load().rsa_mix_release()
+
+
+def rsa_tune(L: int, k: int, n: int, measure: bool = True) -> dict:
+    t = TuneT()
+    _check(load().rsa_tune(L, k, n, 1 if measure else 0, ctypes.byref(t)))
+    return dict(mode="small" if t.mode == RSA_MODE_SMALL else "global", threads=t.threads,
+                rounds_per_check=t.rounds_per_check, ms_per_sample=t.ms_per_sample)
+
+
+def rsa_set_rounds_per_check(h, rounds: int):
+    return _check(load().rsa_set_rounds_per_check(h, rounds))
 
 
 def rsa_results(h, n: int, check: bool = True):

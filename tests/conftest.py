@@ -1,11 +1,16 @@
 import os
 import sys
+import tempfile
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+
+# the autotuner's cache of this test session: a fresh file, not the user's
+os.environ.setdefault("RSA_TUNE_CACHE",
+                      os.path.join(tempfile.mkdtemp(prefix="rsa_tune_"), "tune.jsonl"))
 
 
 def pytest_configure(config):
