@@ -45,6 +45,13 @@ WORKLOADS = {
     "L16384_k4096_x1": dict(L=16384, k=4096, n=1),
 }
 DEFAULT_WORKLOAD = "L32768_k4096_x8"
+# Batches of uneven shapes, run through rsa_run_mix (each shape the way the
+# autotuner picks): groups of (L, k, samples); rank r takes seeds
+# r*n + 1 .. r*n + n of every group.
+MIX_WORKLOADS = {
+    "uneven_k2-8-64-512_x256": [(32, 2, 256), (128, 8, 256), (1024, 64, 256), (8192, 512, 256)],
+    "L64_k4_x100_mix": [(64, 4, 100)],
+}
 METRIC = "jammed samples/s (n_j and n_c per sample, bit-exact to the oracle)"
 
 # Algorithmic bytes per processed lattice cell of each round kernel, from
@@ -346,20 +353,213 @@ def roofline(dom, kstats, work, passes, L, n_cells_round, hbm_peak, peak_kind, s
     return out
 
 
+def mix_arrays(groups, rank):
+    import numpy as np
+    L, k, sd = [], [], []
+    for (gl, gk, gn) in groups:
+        L += [gl] * gn
+        k += [gk] * gn
+        sd += list(range(rank * gn + 1, rank * gn + gn + 1))
+    return np.array(L, np.uint32), np.array(k, np.uint32), np.array(sd, np.uint64)
+
+
+def mix_oracle_rate(groups, threads, reps=1):
+    """Samples/s of the oracle on the whole mix: per group, `threads`
+    samples of its (possibly scaled-down) oracle case on `threads` host
+    threads give its time per sample; the mix takes the sum over groups of
+    samples x time per sample."""
+    import oracle
+    total_t, total_n, secs, parts = 0.0, 0, 0.0, []
+    for (gl, gk, gn) in groups:
+        Lo, ko, scale = oracle_case(gl, gk)
+        t0 = time.perf_counter()
+        for r in range(reps):
+            oracle.samples(Lo, ko, list(range(1 + r * threads, 1 + (r + 1) * threads)),
+                           threads=threads)
+        dt = time.perf_counter() - t0
+        secs += dt
+        per_sample = dt / (reps * threads) * scale
+        total_t += gn * per_sample
+        total_n += gn
+        parts.append(f"L={Lo} k={ko} x{reps * threads}" + (f" (x{scale:.0f} sites)" if scale > 1 else ""))
+    return total_n / total_t, secs, "; ".join(parts)
+
+
+def run_reference_mix(args, groups, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        mix_oracle_rate(groups, cores)
+    rates, t0 = [], time.perf_counter()
+    for _ in range(args.steps):
+        r, _, parts = mix_oracle_rate(groups, cores)
+        rates.append(r)
+    dt = time.perf_counter() - t0
+    rate = sum(rates) / len(rates)
+    n = sum(g[2] for g in groups)
+    sample = (f"per step, {cores} samples per shape on {cores} threads ({parts}); the mix's "
+              f"{n} samples take the sum of samples x time per sample")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "groups": groups},
+        "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+    return 0
+
+
+def run_mix(args, groups, world, rank, local):
+    """A batch of uneven shapes through rsa_run_mix: one step = every group's
+    samples in one call.  Compared with the plain form: each shape's batch on
+    its own handle, one after another."""
+    import numpy as np
+    import torch
+
+    from paper_1810_06800_gb300 import rsa
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    L, k, sd = mix_arrays(groups, rank)
+    n = int(sd.size)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):          # the first call also tunes each shape
+        nj, nc = rsa.rsa_run_mix(L, k, sd, stream)
+    choices = {f"L{gl}_k{gk}": rsa.rsa_tune(gl, gk, gn, measure=False) for (gl, gk, gn) in groups}
+    # ---- device-timed: events on the caller's stream bracket every call
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        nj2, nc2 = rsa.rsa_run_mix(L, k, sd, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    ck = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    wall = max_over_ranks(wall, pg, "cuda")
+    assert np.array_equal(nj, nj2) and np.array_equal(nc, nc2)
+    value = n * world * args.steps / (ms / 1e3)
+    # host arrays in, host results out: the same calls are end to end
+    e2e = n * world * args.steps / wall
+    # ---- plain: each shape's batch on its own handle, one after another
+    rsa.rsa_mix_release()   # the mix's cached handles hold their workspaces
+    barrier()
+    t0 = time.perf_counter()
+    per_shape = {}
+    for (gl, gk, gn) in groups:
+        sel = (L == gl) & (k == gk)
+        lat = rsa.Lattice(gl, gk)
+        t1 = time.perf_counter()
+        pj, pc = lat.run(sd[sel])
+        per_shape[f"L{gl}_k{gk}"] = gn / (time.perf_counter() - t1)
+        lat.close()
+        assert np.array_equal(pj, nj[sel]) and np.array_equal(pc, nc[sel])
+    plain = n / (time.perf_counter() - t0)
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+    # ---- roofline: a profiled pass of the shape with the most cells on its
+    #      own handle (the global path's kernels); the small-lattice groups run
+    #      from shared memory and move no DRAM bytes per cell
+    big = max(groups, key=lambda g: g[0] * g[0] * g[2])
+    sel = (L == big[0]) & (k == big[1])
+    lat = rsa.Lattice(big[0], big[1])
+    lat.run(sd[sel])
+    rsa.rsa_kernel_stats(lat.h)
+    rsa.rsa_work_stats(lat.h)
+    rsa.rsa_profile(lat.h, True)
+    lat.run(sd[sel])
+    kst = {nm: v for nm, v in rsa.rsa_kernel_stats(lat.h).items() if v[1] > 0}
+    work = rsa.rsa_work_stats(lat.h)
+    st = rsa.rsa_sample_stats(lat.h, int(sel.sum()))
+    lat.close()
+    dom = max(kst, key=lambda nm: kst[nm][0])
+    hbm_peak, peak_kind = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    passes = int(np.sum(st["rounds"].astype(np.int64) + 1))
+    roof = roofline(dom, kst, work, passes, big[0], big[0] ** 2, hbm_peak, peak_kind, sm_count,
+                    2070.0)
+    roof["shape"] = f"L={big[0]} k={big[1]}, {big[2]} samples, one profiled pass on its handle"
+    total = sum(v[0] for v in kst.values())
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cores = os.cpu_count() or 1
+        rate, secs, parts = mix_oracle_rate(groups, cores)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"{cores} samples per shape on {cores} threads ({parts}), {secs:.1f} s"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "groups": groups, "samples_per_step": n,
+                   "api": "rsa_run_mix (one call per step)",
+                   "l2": "no flush: working set above 129 MB L2",
+                   "parallelism": f"samples sharded over {world} GPU(s), no collective",
+                   "tuned": choices},
+        "sites_per_s": value * float(np.mean(L.astype(np.float64) ** 2)),
+        "e2e": {"value": e2e, "unit": "samples/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "plain_per_shape_handles": {"value": plain, "unit": "samples/s",
+                                    "per_shape": per_shape},
+        "gpu_launches": None,
+        "roofline": roof,
+        "kernels": {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total, 4)}
+                    for nm, v in kst.items()},
+        "clocks": ck,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + sorted(MIX_WORKLOADS))
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="steps of the separate pass with per-kernel CUDA events")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()
+    if args.workload in MIX_WORKLOADS:
+        if args.impl == "reference":
+            return run_reference_mix(args, MIX_WORKLOADS[args.workload], rank)
+        return run_mix(args, MIX_WORKLOADS[args.workload], world, rank, local)
+    wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl, world, rank)
 
