@@ -14,6 +14,13 @@ device and nothing is copied back but n_j and n_c.
 Every sample's result depends only on (L, k, seed), so a job's results are
 the same alone and in any mix.
 
+A job can be cancelled from the host (``Scheduler.cancel``): its batches not
+yet started are dropped, the ones on the GPU finish and are discarded, and
+the job ends with error "cancelled".  With a journal file, every finished
+batch is appended to it as one JSON line; a scheduler started later with the
+same journal fills a resubmitted job's finished samples from it and runs
+only the rest (restart after a crash or a cancel).
+
 ``python -m paper_1810_06800_gb300.serve`` replays the seeded Poisson job
 stream of ``workloads.served_jobs`` and prints one JSON line with latency
 percentiles and throughput.
@@ -42,7 +49,10 @@ class Job:
     nc: np.ndarray = None
     remaining: int = 0
     t_done: float = None
+    t_start: float = None  # its first batch started on a worker
     error: str = None
+    cancelled: bool = False
+    from_journal: int = 0  # samples filled from the journal
     done_event: threading.Event = field(default_factory=threading.Event)
 
 
@@ -60,8 +70,14 @@ class Scheduler:
     policy can be tested without a GPU."""
 
     def __init__(self, runner, workspace_bytes, budget_bytes: int, workers: int = 4,
-                 max_batch: int = 256, clock=time.perf_counter, max_wait_s: float = 2.0):
+                 max_batch: int = 256, clock=time.perf_counter, max_wait_s: float = 2.0,
+                 journal: str | None = None):
         self.runner = runner
+        self.journal = journal
+        self.journal_lock = threading.Lock()
+        self.journal_done = {}  # (job, L, k, seed) -> {sample: (n_j, n_c)}
+        if journal:
+            self._load_journal()
         self.max_wait_s = max_wait_s
         self.ws_bytes = workspace_bytes
         self.budget = int(budget_bytes)
@@ -94,19 +110,76 @@ class Scheduler:
                               f"budget is {self.budget}")
         return b
 
+    def _load_journal(self):
+        import os
+        if not os.path.exists(self.journal):
+            return
+        with open(self.journal) as f:
+            for line in f:
+                try:
+                    r = json.loads(line)
+                except ValueError:
+                    continue  # a line cut short by a crash
+                done = self.journal_done.setdefault((r["job"], r["L"], r["k"], r["seed"]), {})
+                for i, (a, b) in enumerate(zip(r["nj"], r["nc"])):
+                    done[r["offset"] + i] = (a, b)
+
+    def _journal_batch(self, job: Job, offset: int, nj, nc):
+        line = json.dumps(dict(job=job.job, L=job.L, k=job.k, seed=job.seed, offset=offset,
+                               nj=[int(v) for v in nj], nc=[int(v) for v in nc]))
+        with self.journal_lock, open(self.journal, "a") as f:
+            f.write(line + "\n")
+            f.flush()
+
     def submit(self, job: Job) -> Job:
         job.t_arrival = job.t_arrival or self.clock()
         job.nj = np.zeros(job.n, dtype=np.uint32)
         job.nc = np.zeros(job.n, dtype=np.uint32)
         b = self.batch_size(job.L, job.k, job.n)
-        batches = [Batch(job, o, min(b, job.n - o), self.ws_bytes(job.L, job.k, min(b, job.n - o)))
-                   for o in range(0, job.n, b)]
+        # samples already in the journal are filled, the rest run in batches
+        # over the contiguous ranges still missing
+        known = self.journal_done.get((job.job, job.L, job.k, job.seed), {})
+        todo = []
+        for i in range(job.n):
+            if i in known:
+                job.nj[i], job.nc[i] = known[i]
+            else:
+                todo.append(i)
+        job.from_journal = job.n - len(todo)
+        batches = []
+        i = 0
+        while i < len(todo):
+            j = i
+            while j + 1 < len(todo) and todo[j + 1] == todo[j] + 1 and j + 1 - i < b:
+                j += 1
+            o, m = todo[i], j - i + 1
+            batches.append(Batch(job, o, m, self.ws_bytes(job.L, job.k, m)))
+            i = j + 1
         job.remaining = len(batches)
         with self.cv:
             self.jobs.append(job)
+            if not batches:
+                job.t_done = self.clock()
+                job.done_event.set()
             self.pending.extend(batches)
             self.cv.notify_all()
         return job
+
+    def cancel(self, job: Job) -> None:
+        """Drop the job's batches not yet started; the ones on the GPU finish
+        and are discarded.  The job ends with error "cancelled"."""
+        with self.cv:
+            if job.done_event.is_set():
+                return
+            job.cancelled = True
+            job.error = "cancelled"
+            keep = deque(b for b in self.pending if b.job is not job)
+            job.remaining -= len(self.pending) - len(keep)
+            self.pending = keep
+            if job.remaining == 0:
+                job.t_done = self.clock()
+                job.done_event.set()
+            self.cv.notify_all()
 
     def _take(self):
         """Next batch to run: the oldest pending batch if it fits the free
@@ -143,6 +216,8 @@ class Scheduler:
             if b is None:
                 return
             job = b.job
+            if job.t_start is None:
+                job.t_start = self.clock()
             seeds = np.arange(job.seed + b.offset, job.seed + b.offset + b.n, dtype=np.uint64)
             err = None
             try:
@@ -150,10 +225,14 @@ class Scheduler:
             except Exception as e:  # keep serving; the job reports the error
                 err = f"{type(e).__name__}: {e}"
                 nj = nc = None
+            if not err and self.journal and not job.cancelled:
+                self._journal_batch(job, b.offset, nj, nc)
             with self.cv:
                 self.in_flight_bytes -= b.bytes
                 self.running -= 1
-                if err:
+                if job.cancelled:
+                    pass  # its results are discarded
+                elif err:
                     job.error = job.error or err
                 else:
                     job.nj[b.offset:b.offset + b.n] = nj
@@ -173,10 +252,18 @@ class Scheduler:
                 t.join()
 
     def stats(self):
-        lat = np.array([j.t_done - j.t_arrival for j in self.jobs if j.t_done is not None])
+        done = [j for j in self.jobs if j.t_done is not None and not j.cancelled]
+        lat = np.array([j.t_done - j.t_arrival for j in done])
+        # latency = queue wait (arrival to first batch start) + service
+        wait = np.array([(j.t_start if j.t_start is not None else j.t_done) - j.t_arrival
+                         for j in done])
+
+        def pct(a, q):
+            return float(np.percentile(a, q)) if len(a) else None
         return dict(jobs=len(self.jobs), done=int(len(lat)),
-                    p50_s=float(np.percentile(lat, 50)) if len(lat) else None,
-                    p99_s=float(np.percentile(lat, 99)) if len(lat) else None,
+                    p50_s=pct(lat, 50), p99_s=pct(lat, 99),
+                    wait_p50_s=pct(wait, 50), wait_p99_s=pct(wait, 99),
+                    service_p50_s=pct(lat - wait, 50), service_p99_s=pct(lat - wait, 99),
                     peak_in_flight_bytes=int(self.peak_bytes),
                     peak_concurrent_batches=int(self.peak_running))
 
@@ -198,6 +285,9 @@ class GpuRunner:
         torch, rsa = self.torch, self.rsa
         torch.cuda.set_device(self.device)
         st = self.streams[w]
+        if rsa.rsa_tune(L, k, len(seeds), measure=False)["mode"] == "small":
+            # small lattices: one CTA per sample, no workspace to bind
+            return rsa.rsa_run_small(L, k, seeds, stream=st)
         with torch.cuda.stream(st):
             h = self.handles[w].get((L, k))
             if h is None:
@@ -234,19 +324,19 @@ def gpu_budget(reserve_frac: float = 0.1, device: int = 0) -> int:
 
 
 def make_server(workers: int = 4, budget_bytes: int | None = None, max_batch: int = 256,
-                device: int = 0):
+                device: int = 0, journal: str | None = None):
     from . import rsa
     runner = GpuRunner(workers, device)
     budget = gpu_budget(device=device) if budget_bytes is None else budget_bytes
-    sch = Scheduler(runner, rsa.rsa_workspace_bytes, budget, workers, max_batch)
+    sch = Scheduler(runner, rsa.rsa_workspace_bytes, budget, workers, max_batch, journal=journal)
     sch.gpu_runner = runner
     return sch
 
 
 def replay(jobs, workers: int = 4, budget_bytes: int | None = None, time_scale: float = 1.0,
-           max_batch: int = 256):
+           max_batch: int = 256, journal: str | None = None):
     """Submit jobs at their arrival times (seconds x time_scale) and wait."""
-    sch = make_server(workers, budget_bytes, max_batch)
+    sch = make_server(workers, budget_bytes, max_batch, journal=journal)
     t0 = time.perf_counter()
     subs = []
     for j in jobs:
@@ -268,15 +358,25 @@ def replay(jobs, workers: int = 4, budget_bytes: int | None = None, time_scale: 
     return st, subs
 
 
+def _job_table(subs):
+    return [dict(job=j.job, L=j.L, k=j.k, n=j.n, latency_s=round(j.t_done - j.t_arrival, 4),
+                 wait_s=round((j.t_start or j.t_done) - j.t_arrival, 4)) for j in subs]
+
+
 def main():
     from . import workloads
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--jobs", type=int, default=40)
+    ap.add_argument("--jobs", type=int, default=500)
     ap.add_argument("--rate", type=float, default=4.0, help="mean arrivals per second")
     ap.add_argument("--max-k", type=int, default=1024)
     ap.add_argument("--workers", type=int, default=4)
     ap.add_argument("--max-batch", type=int, default=256)
     ap.add_argument("--master-seed", type=int, default=1810)
+    ap.add_argument("--capacity", action="store_true",
+                    help="first replay every job at once to measure the capacity (jobs/s), "
+                         "then replay the same jobs as a Poisson stream at --load x capacity")
+    ap.add_argument("--load", type=float, default=0.7)
+    ap.add_argument("--journal", default=None, help="JSON-lines journal of finished batches")
     ap.add_argument("--uneven", action="store_true",
                     help="the batched uneven-size workload: k in {2, 8, 64, 512}, L = 16k, "
                          "256 samples each (seeds 1..256), all submitted at once")
@@ -291,11 +391,30 @@ def main():
                                p_c=float((j.k * j.nc / j.L**2).mean())) for j in subs])
         print(json.dumps(st))
         return
+    spec = dict(n=args.jobs, max_k=args.max_k, master_seed=args.master_seed,
+                workers=args.workers, max_batch=args.max_batch,
+                job_mix="k uniform over powers of two in 1..max_k, L/k uniform over "
+                        "{8, 16, 32} (L <= 32768), samples uniform in 16..256")
+    if args.capacity:
+        # closed loop: every job at t = 0; capacity = jobs / wall time
+        jobs0 = workloads.served_jobs(args.jobs, 1.0, args.master_seed, max_k=args.max_k)
+        burst = [dict(j, t=0.0) for j in jobs0]
+        cap_st, _ = replay(burst, args.workers, max_batch=args.max_batch)
+        capacity = args.jobs / cap_st["wall_s"]
+        rate = args.load * capacity
+        jobs = workloads.served_jobs(args.jobs, rate, args.master_seed, max_k=args.max_k)
+        st, subs = replay(jobs, args.workers, max_batch=args.max_batch)
+        st.update(metric="served RSA jobs: latency percentiles and throughput",
+                  capacity=dict(jobs_per_s=capacity, samples_per_s=cap_st["samples_per_s"],
+                                wall_s=cap_st["wall_s"]),
+                  load=args.load, rate_per_s=rate, jobs_spec=spec,
+                  slowest=sorted(_job_table(subs), key=lambda r: -r["latency_s"])[:10])
+        print(json.dumps(st))
+        return
     jobs = workloads.served_jobs(args.jobs, args.rate, args.master_seed, max_k=args.max_k)
-    st, _ = replay(jobs, args.workers, max_batch=args.max_batch)
-    st.update(metric="served RSA jobs: latency percentiles and throughput", jobs_spec=dict(
-        n=args.jobs, rate_per_s=args.rate, max_k=args.max_k, master_seed=args.master_seed,
-        workers=args.workers))
+    st, subs = replay(jobs, args.workers, max_batch=args.max_batch, journal=args.journal)
+    spec.update(rate_per_s=args.rate)
+    st.update(metric="served RSA jobs: latency percentiles and throughput", jobs_spec=spec)
     print(json.dumps(st))
 
 

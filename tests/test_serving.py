@@ -122,3 +122,79 @@ def test_served_jobs_alone_and_in_a_mix_match():
         for i in range(min(3, j.n)):
             wj, wc, _ = oracle.sample(j.L, j.k, j.seed + i)
             assert (int(j.nj[i]), int(j.nc[i])) == (wj, wc)
+
+
+def test_cancel_drops_pending_batches_and_keeps_serving_the_rest():
+    log, lock = [], threading.Lock()
+    sch = serve.Scheduler(_fake_runner(log, lock, delay=0.02), _fake_ws, 64 * 64 * 4, workers=2,
+                          max_batch=2)
+    big = sch.submit(serve.Job(0, 64, 4, 40, 1))       # 20 batches of 2
+    small = sch.submit(serve.Job(1, 32, 2, 6, 50))
+    time.sleep(0.05)                                    # a few batches have started
+    sch.cancel(big)
+    assert big.done_event.wait(10) and small.done_event.wait(10)
+    sch.close()
+    assert big.cancelled and big.error == "cancelled"
+    started = sum(1 for ev, _, b in log if ev == "start" and b == 64 * 64 * 2)
+    assert 1 <= started < 20                            # the rest never ran
+    wj, wc = _expected(32, 2, 50, 6)
+    assert small.error is None and np.array_equal(small.nj, wj) and np.array_equal(small.nc, wc)
+    assert sch.in_flight_bytes == 0 and sch.running == 0
+    assert sch.stats()["done"] == 1                     # latency stats leave the cancelled job out
+
+
+def test_journal_restart_runs_only_the_missing_samples(tmp_path):
+    journal = str(tmp_path / "served.jsonl")
+    log, lock = [], threading.Lock()
+    sch = serve.Scheduler(_fake_runner(log, lock, delay=0.02), _fake_ws, 64 * 64 * 2, workers=1,
+                          max_batch=4, journal=journal)
+    a = sch.submit(serve.Job(0, 64, 4, 24, 1))
+    b = sch.submit(serve.Job(1, 32, 2, 8, 9))
+    time.sleep(0.07)
+    sch.cancel(a)                                       # the "crash": part of job 0 is journaled
+    assert a.done_event.wait(10) and b.done_event.wait(10)
+    sch.close()
+    first_batches = sum(1 for ev, _, _ in log if ev == "start")
+    # restart with the same journal: finished samples come from it
+    log2 = []
+    sch2 = serve.Scheduler(_fake_runner(log2, lock), _fake_ws, 64 * 64 * 2, workers=1,
+                           max_batch=4, journal=journal)
+    a2 = sch2.submit(serve.Job(0, 64, 4, 24, 1))
+    b2 = sch2.submit(serve.Job(1, 32, 2, 8, 9))
+    assert a2.done_event.wait(10) and b2.done_event.wait(10)
+    sch2.close()
+    for j in (a2, b2):
+        wj, wc = _expected(j.L, j.k, j.seed, j.n)
+        assert j.error is None and np.array_equal(j.nj, wj) and np.array_equal(j.nc, wc)
+    assert b2.from_journal == 8 and 0 < a2.from_journal < 24
+    ran = sum(n for ev, _, n in log2 if ev == "start") // (64 * 64)
+    assert ran == 24 - a2.from_journal                  # only the missing samples ran
+    assert first_batches >= 1
+
+
+@pytest.mark.gpu
+def test_served_large_k_jobs_alone_and_in_a_mix_match():
+    # shapes of the served stream's upper range (k up to 1024, L/k in
+    # {8, 16, 32}) next to small-lattice jobs run one CTA per sample
+    import oracle
+    from paper_1810_06800_gb300 import rsa
+    specs = [(8192, 1024, 2, 1), (2048, 256, 3, 5), (1024, 64, 4, 7), (64, 4, 20, 3),
+             (32, 1, 10, 9), (16, 2, 12, 4)]
+    alone = []
+    for L, k, n, seed in specs:
+        lat = rsa.Lattice(L, k)
+        alone.append(lat.run(np.arange(seed, seed + n, dtype=np.uint64)))
+        lat.close()
+    sch = serve.make_server(workers=4, budget_bytes=16 << 30, max_batch=4)
+    jobs = [sch.submit(serve.Job(i, *sp)) for i, sp in enumerate(specs)]
+    for j in jobs:
+        assert j.done_event.wait(300)
+    sch.close()
+    sch.gpu_runner.close()
+    for (aj, ac), j in zip(alone, jobs):
+        assert j.error is None
+        assert np.array_equal(aj, j.nj) and np.array_equal(ac, j.nc)
+    for j in jobs:
+        if j.L <= 1024:
+            wj, wc = oracle.samples(j.L, j.k, list(range(j.seed, j.seed + j.n)))
+            assert np.array_equal(j.nj, wj.astype(np.uint32)) and np.array_equal(j.nc, wc.astype(np.uint32))
