@@ -6,6 +6,7 @@
 // drop out.  The data-dependent loops (greedy rounds, bisection probes) are
 // driven from the host with one small device->host read per few iterations.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cstddef>
@@ -26,6 +27,13 @@
 using namespace rsak;
 
 namespace {
+
+// An NVTX range for the lifetime of a scope (a no-op unless a profiler that
+// collects NVTX ranges is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 thread_local std::string g_err;
 
@@ -565,6 +573,7 @@ int run_chunk(rsa_t* h, rsa_t::GraphSlot& gs, cudaStream_t stream, u32 n, B body
 
 int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaStream_t stream) {
   if (n == 0) return fail(RSA_EINVAL, "n_samples must be >= 1");
+  NvtxRange run_range("rsa_run");
   int rc;
   CUDA_TRY(cudaGetDevice(&h->device));
   if (!h->h_counter) CUDA_TRY(cudaMallocHost(&h->h_counter, 64));
@@ -700,6 +709,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
              d_counter);
     }
   };
+  {
+  NvtxRange rounds_range("greedy rounds");
   for (u32 chunks = 0;;) {
     const u32 burst = chunks == 0 ? h->round_chunks_hint : 1;
     for (u32 i = 0; i < burst; ++i, ++chunks)
@@ -712,6 +723,8 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
       break;
     }
   }
+  }
+  NvtxRange wrap_range("contact graph and first-wrap search");
   // contact graph of the jammed lattice
   {
     // rows per sample spread over enough blocks to fill the GPU across the batch

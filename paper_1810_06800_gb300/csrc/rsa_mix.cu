@@ -12,6 +12,7 @@
 // Everything here runs the library's own kernels through its public calls;
 // results never depend on the choices made (tested).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <sys/stat.h>
 
 #include <algorithm>
@@ -75,6 +76,8 @@ extern "C" int rsa_run_small(const uint32_t* L, const uint32_t* k, const uint64_
   if (!L || !k || !seeds || !n_j || !n_c || n == 0)
     return set_error(RSA_EINVAL, "rsa_run_small: null array or n == 0");
   if (threads == 0) threads = 512;
+  nvtxRangePushA("rsa_run_small");
+  struct Pop { ~Pop() { nvtxRangePop(); } } pop;
   if (threads % 32 || threads > 1024) return set_error(RSA_EINVAL, "threads must be 32 .. 1024, a multiple of 32");
   std::vector<SmallJob> jobs(n);
   uint32_t Lm = 0;
@@ -366,6 +369,8 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
   for (uint32_t i = 0; i < n; ++i)
     if (!(k[i] >= 1 && k[i] <= L[i] && L[i] <= 32768))
       return set_error(RSA_EINVAL, "rsa_run_mix: sample " + std::to_string(i) + " needs 1 <= k <= L <= 32768");
+  nvtxRangePushA("rsa_run_mix");
+  struct Pop { ~Pop() { nvtxRangePop(); } } pop;
   int dev = 0;
   MIX_CUDA(cudaGetDevice(&dev));
   const char* at = std::getenv("RSA_AUTOTUNE");
