@@ -674,6 +674,13 @@ def main():
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     sm_mhz = float(json.load(open(pk))["sm_max_mhz"]) if os.path.exists(pk) else 2070.0
     roof = roofline(dom, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz)
+    # the same figures for every round kernel with a byte model
+    roof_all = {}
+    for nm in ours:
+        if nm in KERNEL_STEPS:
+            r = roofline(nm, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz)
+            roof_all[nm] = {k2: r.get(k2) for k2 in ("achieved", "frac", "alg_bytes_per_cell",
+                                                      "avg_launch_ms", "traffic")}
     total_ms = sum(x[0] for x in ours.values())
     kernel_table = {nm: {"ms": round(v[0], 3), "launches": v[1],
                          "share": round(v[0] / total_ms, 4)} for nm, v in ours.items()}
@@ -706,6 +713,7 @@ def main():
                                         "samples": plain_n},
         "gpu_launches": gpu_launches,
         "roofline": roof,
+        "rooflines": roof_all,
         "profiled_pass": {"steps": psteps, "ms_per_step": prof_ms / psteps,
                           "note": "per-kernel shares and the roofline come from this pass; "
                                   "value is timed without per-launch events"},
