@@ -551,6 +551,10 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(MIX_WORKLOADS))
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="steps of the separate pass with per-kernel CUDA events")
+    ap.add_argument("--window-threads", type=int, default=0,
+                    help="CTA size of the long-k window pass (128 or 256; 0 = the library default)")
+    ap.add_argument("--rounds-per-check", type=int, default=0,
+                    help="greedy rounds per captured chunk (0 = the library default)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -580,6 +584,10 @@ def main():
     stream = torch.cuda.current_stream()
     lat = rsa.Lattice(L, k)
     h = lat.h
+    if args.window_threads:
+        rsa.rsa_set_window_threads(h, args.window_threads)
+    if args.rounds_per_check:
+        rsa.rsa_set_rounds_per_check(h, args.rounds_per_check)
 
     def barrier():
         if pg is not None:
@@ -705,7 +713,9 @@ def main():
                    "seeds": f"rank*{n}+1..rank*{n}+{n}",
                    "l2": "no flush: working set %.1f GB per step > 129 MB L2" % (
                        rsa.rsa_workspace_bytes(L, k, n) / 1e9),
-                   "parallelism": f"samples sharded over {world} GPU(s), no collective"},
+                   "parallelism": f"samples sharded over {world} GPU(s), no collective",
+                   "window_threads": args.window_threads or None,
+                   "rounds_per_check": args.rounds_per_check or None},
         "sites_per_s": value * L * L,
         "e2e": {"value": e2e, "unit": "samples/s", "h2d_bytes_per_step": int(8 * n),
                 "d2h_bytes_per_step": int(128 * n)},

@@ -124,11 +124,12 @@ void rsa_mix_release(void);
 /* How a shape runs: RSA_MODE_SMALL (one CTA per sample, `threads` per CTA)
  * or RSA_MODE_GLOBAL (the tiled / long-k / general kernels over the whole
  * batch, `rounds_per_check` greedy rounds per captured graph chunk and host
- * check).  ms_per_sample is the time measured when the choice was made. */
+ * check, `window_threads` threads per CTA of the long-k window pass).
+ * ms_per_sample is the time measured when the choice was made. */
 #define RSA_MODE_GLOBAL 0
 #define RSA_MODE_SMALL 1
 typedef struct {
-  uint32_t mode, threads, rounds_per_check;
+  uint32_t mode, threads, rounds_per_check, window_threads;
   double ms_per_sample;
 } rsa_tune_t;
 
@@ -140,12 +141,20 @@ typedef struct {
  * the global path at 2 / 4 / 8 rounds per check) is timed once on seeds
  * 1 .. n (at most 8 GB of workspace) and the fastest is kept and appended
  * to the file; otherwise a default is returned (small mode at 512 threads
- * where it fits, else the global path at 4). */
+ * where it fits, else the global path at 4 rounds per check and 256-thread
+ * windows).  The long-k window pass is also timed at 128 threads per CTA
+ * (twice the cells per thread) where the shape allows it. */
 int rsa_tune(uint32_t L, uint32_t k, uint32_t n, int measure, rsa_tune_t *out);
 
 /* Greedy rounds per captured graph chunk and host check of later runs on
  * this handle (1 .. 64, default 4).  Results do not depend on it. */
 int rsa_set_rounds_per_check(rsa_t *h, uint32_t rounds);
+
+/* CTA size of the long-k window pass of later runs on this handle: 256
+ * (default) or 128 threads per CTA, each thread then holding twice as many
+ * cells of the span.  128 needs the argmin-offset long-k path with spans of
+ * 2048 or 4096 cells (RSA_EINVAL otherwise).  Results do not depend on it. */
+int rsa_set_window_threads(rsa_t *h, uint32_t threads);
 
 /* Copy the last run's results to caller-owned host arrays of length n
  * (n <= samples of the last run; either pointer may be NULL).  Synchronises

@@ -306,6 +306,7 @@ struct rsa {
   // run launches that many before its first device->host check
   u32 round_chunks_hint = 1, probe_chunks_hint = 1;
   u32 round_check = ROUND_CHECK;  // greedy rounds per graph chunk / host check
+  u32 lw_threads = 256;           // CTA size of the long-k window pass (256 or 128)
   // test-only lowered caps of the device loops (0 = default; rsa_test_caps)
   u32 t_round = 0, t_uf = 0, t_probe = 0, t_edges = 0;
   struct GraphSlot {
@@ -313,7 +314,7 @@ struct rsa {
     const void* ws = nullptr;
     u32 n = 0;
     bool keys = false;
-    u32 caps[5] = {0, 0, 0, 0, 0};  // test caps and rounds per chunk baked into the graph
+    u32 caps[6] = {0, 0, 0, 0, 0, 0};  // caps, rounds per chunk, window CTA size in the graph
     unsigned long long launches[32] = {};
   } g_round, g_probe;
 };
@@ -443,19 +444,33 @@ cudaError_t launch_cluster(rsa_t* h, int kind, void (*kernel)(KArgs...), dim3 gr
   return e;
 }
 
+template <int F, int NT>
+cudaError_t launch_lwin_nt(rsa_t* h, Group g, const Geometry& G, const u32* occw, const u32* occT,
+                           u16* out, u8* lflag, u32 n, cudaStream_t st) {
+  const dim3 grid(g.L * G.lw_cfg.nc, n), block(NT);
+  const int kind = F == 0 ? KD_LWIN_H : KD_LWIN_V;
+  const u32 nc = G.lw_cfg.nc, C = G.lw_cfg.P / NT;
+  if constexpr (NT == 128) {
+    if (C == 32) return launch_cluster(h, kind, k_lwin<F, 32, 128>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+    return launch_cluster(h, kind, k_lwin<F, 16, 128>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+  } else {
+    switch (C) {
+      case 1: return launch_cluster(h, kind, k_lwin<F, 1, 256>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+      case 2: return launch_cluster(h, kind, k_lwin<F, 2, 256>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+      case 4: return launch_cluster(h, kind, k_lwin<F, 4, 256>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+      case 8: return launch_cluster(h, kind, k_lwin<F, 8, 256>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+      default: return launch_cluster(h, kind, k_lwin<F, 16, 256>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
+    }
+  }
+}
+
+// The window pass with the handle's CTA size: 256 threads, or 128 threads
+// with twice the cells per thread (spans of 2048 or 4096 cells).
 template <int F>
 cudaError_t launch_lwin(rsa_t* h, Group g, const Geometry& G, const u32* occw, const u32* occT,
                         u16* out, u8* lflag, u32 n, cudaStream_t st) {
-  const dim3 grid(g.L * G.lw_cfg.nc, n), block(LW_THREADS);
-  const int kind = F == 0 ? KD_LWIN_H : KD_LWIN_V;
-  const u32 nc = G.lw_cfg.nc;
-  switch (G.lw_C) {
-    case 1: return launch_cluster(h, kind, k_lwin<F, 1>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
-    case 2: return launch_cluster(h, kind, k_lwin<F, 2>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
-    case 4: return launch_cluster(h, kind, k_lwin<F, 4>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
-    case 8: return launch_cluster(h, kind, k_lwin<F, 8>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
-    default: return launch_cluster(h, kind, k_lwin<F, 16>, grid, block, 0, st, nc, g, G.lw_cfg, occw, occT, out, lflag);
-  }
+  if (h->lw_threads == 128) return launch_lwin_nt<F, 128>(h, g, G, occw, occT, out, lflag, n, st);
+  return launch_lwin_nt<F, 256>(h, g, G, occw, occT, out, lflag, n, st);
 }
 
 int launch_check(const char* what) {
@@ -535,7 +550,8 @@ int run_chunk(rsa_t* h, rsa_t::GraphSlot& gs, cudaStream_t stream, u32 n, B body
     body(stream);
     return launch_check("chunk launches");
   }
-  const u32 caps[5] = {h->t_round, h->t_uf, h->t_probe, h->t_edges, h->round_check};
+  const u32 caps[6] = {h->t_round, h->t_uf, h->t_probe, h->t_edges, h->round_check,
+                       h->lw_threads};
   if (!(gs.exec && gs.ws == h->ws && gs.n == n && gs.keys == h->with_keys &&
         std::memcmp(gs.caps, caps, sizeof(caps)) == 0)) {
     drop_graph(gs);
@@ -1104,6 +1120,15 @@ int rsa_set_rounds_per_check(rsa_t* h, uint32_t rounds) {
   if (rounds < 1 || rounds > 64) return fail(RSA_EINVAL, "rounds per check must be in 1 .. 64");
   if (rounds != h->round_check) h->round_chunks_hint = 1;
   h->round_check = rounds;
+  return 0;
+}
+
+int rsa_set_window_threads(rsa_t* h, uint32_t threads) {
+  if (!h) return fail(RSA_EINVAL, "null handle");
+  if (threads != 256 && threads != 128) return fail(RSA_EINVAL, "window CTA size must be 128 or 256");
+  if (threads == 128 && !(h->geo.lw && (h->geo.lw_cfg.P == 4096 || h->geo.lw_cfg.P == 2048)))
+    return fail(RSA_EINVAL, "128-thread windows need the long-k offset path with spans of 2048 or 4096 cells");
+  h->lw_threads = threads;
   return 0;
 }
 

@@ -68,6 +68,7 @@ __device__ __forceinline__ void kp_min(u64& a, u32& pa, u64 b, u32 pb) {
 __device__ __forceinline__ void lw_block_scans(u64 a, u32 pa, u32 m, u64& ep, u32& epp, u64& es,
                                                u32& esp, u64* wtf, u32* wtfp, u64* wtb,
                                                u32* wtbp) {
+  // (m is at most the block's thread count: a k-block never spans CTAs)
   const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 wd = m < 32 ? m : 32, li = lane & (wd - 1);
   u64 f = a, b = a;
@@ -105,17 +106,18 @@ __device__ __forceinline__ void lw_block_scans(u64 a, u32 pa, u32 m, u64& ep, u3
 // nc + r] bit 0: span r of the line has no live anchor (stays so).
 // Minima carry the line position of their candidate, so the offset of the
 // winner is cell - position; no priority is inverted.
-template <int F, int C>
-__global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const u32* occw,
-                                                     const u32* occT, u16* cout, u8* lflag) {
+template <int F, int C, int NT>
+__global__ void __launch_bounds__(NT) k_lwin(Group g, LwinCfg lc, const u32* occw,
+                                             const u32* occT, u16* cout, u8* lflag) {
   namespace cg = cooperative_groups;
-  __shared__ u64 Qk[C][LW_THREADS];      // suffix minimum at element e of chunk t: [e][t]
-  __shared__ u16 Qp[C][LW_THREADS];      // its candidate's position on the line
-  __shared__ u32 w[LW_THREADS + 2];      // staged occupancy words
-  __shared__ u32 nw[LW_THREADS + 2];     // first occupied position at / after word i
-  __shared__ u32 wmin[LW_THREADS / 32];
-  __shared__ u64 wtf[LW_THREADS / 32], wtb[LW_THREADS / 32];
-  __shared__ u32 wtfp[LW_THREADS / 32], wtbp[LW_THREADS / 32];
+  constexpr u32 WPT = (256 + NT - 1) / NT;  // occupancy words staged per thread
+  __shared__ u64 Qk[C][NT];      // suffix minimum at element e of chunk t: [e][t]
+  __shared__ u16 Qp[C][NT];      // its candidate's position on the line
+  __shared__ u32 w[256 + 2];     // staged occupancy words
+  __shared__ u32 nw[256 + 2];    // first occupied position at / after word i
+  __shared__ u32 wmin[NT / 32];
+  __shared__ u64 wtf[NT / 32], wtb[NT / 32];
+  __shared__ u32 wtfp[NT / 32], wtbp[NT / 32];
   cg::cluster_group cl = cg::this_cluster();
   const u32 nc = lc.nc, r = cl.block_rank();
   const u32 line = blockIdx.x / nc, s = blockIdx.y;
@@ -136,19 +138,27 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
   u64 ep = KEY_NONE, es = KEY_NONE;
   u32 epp = LW_SENT, esp = LW_SENT;
   if (!own_dead) {
-    // occupancy words of [x0, x0 + P + k - 1), around the torus
+    // occupancy words of [x0, x0 + P + k - 1), around the torus; thread t
+    // stages words t WPT .. t WPT + WPT - 1
     const u32 nwords = (P + k + 30) / 32;  // <= 256: P, k <= 4096
     const u32* bits = (F == 0 ? occw : occT) + ((size_t)s * L + line) * T;
-    u32 fst = LW_INF;
-    if (tid < nwords) {
-      u32 wi = x0 / 32 + tid;
-      while (wi >= T) wi -= T;
-      const u32 wdd = bits[wi];
-      w[tid] = wdd;
-      if (wdd) fst = tid * 32 + __ffs(wdd) - 1;
+    u32 fst[WPT];
+#pragma unroll
+    for (u32 j = 0; j < WPT; ++j) {
+      const u32 i = tid * WPT + j;
+      fst[j] = LW_INF;
+      if (i < nwords) {
+        u32 wi = x0 / 32 + i;
+        while (wi >= T) wi -= T;
+        const u32 wdd = bits[wi];
+        w[i] = wdd;
+        if (wdd) fst[j] = i * 32 + __ffs(wdd) - 1;
+      }
     }
     // nw[i] = min over words j >= i of their first occupied position
-    u32 sm = fst;
+#pragma unroll
+    for (int j = (int)WPT - 2; j >= 0; --j) fst[j] = min(fst[j], fst[j + 1]);
+    u32 sm = fst[0];
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const u32 o = __shfl_down_sync(FULL, sm, d);
@@ -156,9 +166,14 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
     }
     if (lane == 0) wmin[warp] = sm;
     __syncthreads();
-    for (u32 w2 = warp + 1; w2 < LW_THREADS / 32; ++w2) sm = min(sm, wmin[w2]);
-    nw[tid] = sm;
-    if (tid == 0) nw[LW_THREADS] = LW_INF;
+    // what follows this thread's words: later lanes of the warp, later warps
+    u32 after = __shfl_down_sync(FULL, sm, 1);
+    if (lane == 31) after = LW_INF;
+    for (u32 w2 = warp + 1; w2 < NT / 32; ++w2) after = min(after, wmin[w2]);
+#pragma unroll
+    for (u32 j = 0; j < WPT; ++j)
+      if (tid * WPT + j < 256) nw[tid * WPT + j] = min(fst[j], after);
+    if (tid == 0) nw[256] = LW_INF;
     __syncthreads();
     // the chunk's candidates.  k > 32, so a candidate at q is live iff no
     // cell of its own word from q on is occupied (q is past the word's last
@@ -206,10 +221,10 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
     const u64* QkR = rp == r ? &Qk[0][0] : cl.map_shared_rank(&Qk[0][0], rp);
     const u16* QpR = rp == r ? &Qp[0][0] : cl.map_shared_rank(&Qp[0][0], rp);
     const int ca = cb, cc = cb + 1;
-    const u64* ka = ca >= 0 ? &Qk[0][ca] : QkR + (ca + (int)LW_THREADS);
-    const u16* pa = ca >= 0 ? &Qp[0][ca] : QpR + (ca + (int)LW_THREADS);
-    const u64* kc = cc >= 0 ? &Qk[0][cc] : QkR + (cc + (int)LW_THREADS);
-    const u16* pc = cc >= 0 ? &Qp[0][cc] : QpR + (cc + (int)LW_THREADS);
+    const u64* ka = ca >= 0 ? &Qk[0][ca] : QkR + (ca + (int)NT);
+    const u16* pa = ca >= 0 ? &Qp[0][ca] : QpR + (ca + (int)NT);
+    const u64* kc = cc >= 0 ? &Qk[0][cc] : QkR + (cc + (int)NT);
+    const u16* pc = cc >= 0 ? &Qp[0][cc] : QpR + (cc + (int)NT);
     const bool closes = tid % m == m - 1;  // the chunk's last cell ends its k-block
     u64 rk = ep;
     u32 rq = epp;
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(LW_THREADS) k_lwin(Group g, LwinCfg lc, const 
       u32 mq = rq;
       const int el = (e + 1) % C;
       if (e < C - 1) {
-        kp_min(mk, mq, ka[el * LW_THREADS], pa[el * LW_THREADS]);
+        kp_min(mk, mq, ka[el * NT], pa[el * NT]);
       } else if (!closes) {
         kp_min(mk, mq, kc[0], pc[0]);
       }

@@ -176,7 +176,7 @@ void tune_load_locked() {
   char buf[1024];
   while (std::fgets(buf, sizeof(buf), f)) {
     const std::string line(buf);
-    std::string gpu, L, k, n, mode, thr, rpc, ms;
+    std::string gpu, L, k, n, mode, thr, rpc, ms, wt;
     if (!json_field(line, "gpu", &gpu) || !json_field(line, "L", &L) || !json_field(line, "k", &k) ||
         !json_field(line, "n", &n) || !json_field(line, "mode", &mode) ||
         !json_field(line, "threads", &thr) || !json_field(line, "rounds_per_check", &rpc) ||
@@ -187,6 +187,8 @@ void tune_load_locked() {
     c.threads = (uint32_t)std::strtoul(thr.c_str(), nullptr, 10);
     c.rounds_per_check = (uint32_t)std::strtoul(rpc.c_str(), nullptr, 10);
     c.ms_per_sample = std::strtod(ms.c_str(), nullptr);
+    c.window_threads = json_field(line, "window_threads", &wt)
+                           ? (uint32_t)std::strtoul(wt.c_str(), nullptr, 10) : 256u;
     g_tune[std::make_tuple(gpu, (uint32_t)std::strtoul(L.c_str(), nullptr, 10),
                            (uint32_t)std::strtoul(k.c_str(), nullptr, 10),
                            (uint32_t)std::strtoul(n.c_str(), nullptr, 10))] = c;
@@ -207,9 +209,10 @@ void tune_store_locked(const std::string& gpu, uint32_t L, uint32_t k, uint32_t 
   if (!f) return;  // the in-memory table still holds it
   std::fprintf(f,
                "{\"gpu\": \"%s\", \"L\": %u, \"k\": %u, \"n\": %u, \"mode\": \"%s\", "
-               "\"threads\": %u, \"rounds_per_check\": %u, \"ms_per_sample\": %.6g}\n",
+               "\"threads\": %u, \"rounds_per_check\": %u, \"window_threads\": %u, "
+               "\"ms_per_sample\": %.6g}\n",
                gpu.c_str(), L, k, nb, c.mode == RSA_MODE_SMALL ? "small" : "global", c.threads,
-               c.rounds_per_check, c.ms_per_sample);
+               c.rounds_per_check, c.window_threads, c.ms_per_sample);
   std::fclose(f);
 }
 
@@ -225,6 +228,7 @@ rsa_tune_t default_config(uint32_t L, uint32_t k) {
   } else {
     c.mode = RSA_MODE_GLOBAL;
     c.rounds_per_check = 4;
+    c.window_threads = 256;
   }
   return c;
 }
@@ -253,6 +257,7 @@ int time_config(uint32_t L, uint32_t k, uint32_t nb, const rsa_tune_t& c, cudaSt
     rsa_t* h = nullptr;
     if ((rc = rsa_create(L, k, 1, &h))) return rc;
     rc = rsa_set_rounds_per_check(h, c.rounds_per_check);
+    if (!rc && c.window_threads) rc = rsa_set_window_threads(h, c.window_threads);
     for (int rep = 0; rep < 2 && !rc; ++rep) {
       const double t0 = now_ms();
       rc = rsa_run_seeds(h, seeds.data(), nb, st);
@@ -301,12 +306,24 @@ extern "C" int rsa_tune(uint32_t L, uint32_t k, uint32_t n, int measure, rsa_tun
       c.threads = t;
       cands.push_back(c);
     }
-  for (uint32_t r : {2u, 4u, 8u}) {
-    rsa_tune_t c{};
-    c.mode = RSA_MODE_GLOBAL;
-    c.rounds_per_check = r;
-    cands.push_back(c);
+  // the 128-thread window pass exists only for some shapes: ask a handle
+  bool w128 = false;
+  {
+    rsa_t* h = nullptr;
+    if (rsa_create(L, k, 1, &h) == 0) {
+      w128 = rsa_set_window_threads(h, 128) == 0;
+      rsa_destroy(h);
+    }
   }
+  for (uint32_t r : {2u, 4u, 8u})
+    for (uint32_t wt : {256u, 128u}) {
+      if (wt == 128 && !w128) continue;
+      rsa_tune_t c{};
+      c.mode = RSA_MODE_GLOBAL;
+      c.rounds_per_check = r;
+      c.window_threads = wt;
+      cands.push_back(c);
+    }
   cudaStream_t st = nullptr;
   MIX_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   rsa_tune_t best = *out;
@@ -382,7 +399,7 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
   uint32_t small_threads = 512;
   uint64_t small_work = 0;
   struct Job {
-    uint32_t L, k, rpc;
+    uint32_t L, k, rpc, wt;
     const std::vector<uint32_t>* idx;
   };
   std::vector<Job> global;
@@ -399,7 +416,7 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
       }
     } else {
       global.push_back(Job{gkv.first.first, gkv.first.second, c.rounds_per_check ? c.rounds_per_check : 4u,
-                           &gkv.second});
+                           c.window_threads ? c.window_threads : 256u, &gkv.second});
     }
   }
   // everything already queued on the caller's stream comes first
@@ -428,6 +445,7 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
       std::vector<uint32_t> a(m), b(m);
       for (uint32_t i = 0; i < m; ++i) sd[i] = seeds[(*J.idx)[i]];
       int rc2 = rsa_set_rounds_per_check(slot->h, J.rpc);
+      if (rsa_set_window_threads(slot->h, J.wt)) rsa_set_window_threads(slot->h, 256);
       if (!rc2) rc2 = rsa_run_seeds(slot->h, sd.data(), m, slot->st);
       if (!rc2) rc2 = rsa_results(slot->h, a.data(), b.data(), m);
       if (!rc2) cudaEventRecord(slot->done, slot->st);

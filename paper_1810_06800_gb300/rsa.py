@@ -24,6 +24,7 @@ SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_
            "rsa_sample_stats", "rsa_contacts", "rsa_cluster_sizes", "rsa_wrap_dirs", "rsa_accepted",
            "rsa_workspace_bytes", "rsa_bind_workspace", "rsa_test_caps",
            "rsa_run_small", "rsa_run_mix", "rsa_tune", "rsa_set_rounds_per_check",
+           "rsa_set_window_threads",
            "rsa_mix_release", "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
@@ -36,7 +37,8 @@ RSA_MODE_GLOBAL, RSA_MODE_SMALL = 0, 1
 class TuneT(ctypes.Structure):
     """rsa_tune_t: how a shape runs (see include/rsa.h)."""
     _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32),
-                ("rounds_per_check", ctypes.c_uint32), ("ms_per_sample", ctypes.c_double)]
+                ("rounds_per_check", ctypes.c_uint32), ("window_threads", ctypes.c_uint32),
+                ("ms_per_sample", ctypes.c_double)]
 
 
 class RSAError(RuntimeError):
@@ -77,6 +79,7 @@ def load():
     lib.rsa_run_mix.argtypes = [vp, vp, vp, u32, vp, vp, vp]
     lib.rsa_tune.argtypes = [u32, u32, u32, ip, ctypes.POINTER(TuneT)]
     lib.rsa_set_rounds_per_check.argtypes = [vp, u32]
+    lib.rsa_set_window_threads.argtypes = [vp, u32]
     lib.rsa_mix_release.argtypes = []
     lib.rsa_destroy.argtypes = [vp]
     lib.rsa_destroy.restype = None
@@ -182,11 +185,16 @@ def rsa_tune(L: int, k: int, n: int, measure: bool = True) -> dict:
     t = TuneT()
     _check(load().rsa_tune(L, k, n, 1 if measure else 0, ctypes.byref(t)))
     return dict(mode="small" if t.mode == RSA_MODE_SMALL else "global", threads=t.threads,
-                rounds_per_check=t.rounds_per_check, ms_per_sample=t.ms_per_sample)
+                rounds_per_check=t.rounds_per_check, window_threads=t.window_threads,
+                ms_per_sample=t.ms_per_sample)
 
 
 def rsa_set_rounds_per_check(h, rounds: int):
     return _check(load().rsa_set_rounds_per_check(h, rounds))
+
+
+def rsa_set_window_threads(h, threads: int):
+    return _check(load().rsa_set_window_threads(h, threads))
 
 
 def rsa_results(h, n: int, check: bool = True):

@@ -139,3 +139,34 @@ def test_rounds_per_check_does_not_change_results():
         nj, nc = lat.run(seeds)
         lat.close()
         assert np.array_equal(nj, wj) and np.array_equal(nc, wc)
+
+
+@pytest.mark.parametrize("L,k", [(8192, 512), (2048, 256), (4096, 4096)])
+def test_window_cta_size_does_not_change_results(L, k):
+    seeds = [1, 2] if L == 8192 else [3, 4, 5]
+    out = []
+    for wt in (256, 128):
+        lat = rsa.Lattice(L, k)
+        rsa.rsa_set_window_threads(lat.h, wt)
+        out.append(lat.run(seeds))
+        acc = [lat.accepted(i) for i in range(len(seeds))]
+        out.append(acc)
+        lat.close()
+    assert np.array_equal(out[0][0], out[2][0]) and np.array_equal(out[0][1], out[2][1])
+    for a, b in zip(out[1], out[3]):
+        assert np.array_equal(a, b)
+    if L == 8192:
+        gold = _golden(8192, 512)
+        for i, s in enumerate(seeds):
+            assert (int(out[2][0][i]), int(out[2][1][i])) == (gold[s]["n_j"], gold[s]["n_c"])
+    else:
+        wj, wc = _oracle(L, k, seeds)
+        assert np.array_equal(out[2][0], wj) and np.array_equal(out[2][1], wc)
+
+
+def test_window_cta_size_is_rejected_where_it_does_not_apply():
+    lat = rsa.Lattice(1024, 32)       # tile path
+    with pytest.raises(rsa.RSAError):
+        rsa.rsa_set_window_threads(lat.h, 128)
+    rsa.rsa_set_window_threads(lat.h, 256)
+    lat.close()
