@@ -207,10 +207,10 @@ Layout layout_of(u32 L, u32 k, u32 n, bool with_keys, const Geometry& G) {
   // acceptance masks: win / first / last, rows then the transposed layout
   l.masks = take(lw ? 6 * (n * LL / 8) : 0);
   // dead flags: per 32 x 32 tile (tile path); per line segment (or span) of
-  // each orientation, then per 32 x 32 code tile (long-k path)
-  // (32 x 16 code strips on the argmin-offset path)
+  // each orientation, then per 32 x 32 code tile (long-k path; 32 x 32
+  // combine squares on the argmin-offset path)
   const u32 nseg = lw ? G.lw_cfg.nc : G.lc.nseg;
-  const size_t ncode = lw ? 2ull * G.tc.T2 : G.tc.T2;
+  const size_t ncode = G.tc.T2;
   l.dead = take(G.tile ? (size_t)n * G.tc.T2
                        : G.line ? (size_t)n * (2ull * L * nseg + ncode) : 0);
   l.owner = take(n * LL * 4);
@@ -618,7 +618,7 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   } else if (G.line) {
     CUDA_TRY(cudaMemsetAsync(b + l.occw, 0, (size_t)n * LL / 8, stream));
     CUDA_TRY(cudaMemsetAsync(b + l.occT, 0, (size_t)n * LL / 8, stream));
-    const size_t ncode = use_lw ? 2ull * G.tc.T2 : G.tc.T2;
+    const size_t ncode = G.tc.T2;
     CUDA_TRY(cudaMemsetAsync(b + l.dead, 0, (size_t)n * (2ull * h->L * line_nseg + ncode),
                              stream));
   } else {
@@ -680,7 +680,7 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
         const AccMasks mh{mk, mk + mw, mk + 2 * mw}, mv{mk + 3 * mw, mk + 4 * mw, mk + 5 * mw};
         if (launch_lwin<0>(h, g, G, occw, occT, cH, lflag, n, st) != cudaSuccess) body_rc = RSA_ECUDA;
         if (launch_lwin<1>(h, g, G, occw, occT, cV, lflag, n, st) != cudaSuccess) body_rc = RSA_ECUDA;
-        launch(h, KD_LCOMB, k_lcomb, dim3((2 * G.tc.T2 + LC_WARPS - 1) / LC_WARPS, n),
+        launch(h, KD_LCOMB, k_lcomb, dim3((G.tc.T2 + LC_WARPS - 1) / LC_WARPS, n),
                dim3(LC_WARPS * 32), sizeof(LcombSmem), st, g, (const u16*)cH, (const u16*)cV, mh,
                mv, cdead);
         const dim3 ag(h->L * line_nseg, n);

@@ -9,8 +9,8 @@
 //               occupancy), stored transposed;
 //   k_lcomb     per cell, the smaller of the two winners' priorities (both
 //               recomputed from their anchors) picks the final winner, kept
-//               as bit masks in its orientation's layout (32 x 16 strips, one
-//               warp each);
+//               as bit masks in its orientation's layout (32 x 32 squares,
+//               one warp each);
 //   k_lacc<F>   acceptance along lines from the masks, 32 anchors per word
 //               operation, and the accepted k-mers' nodes, occupancy and
 //               owners.
@@ -111,8 +111,10 @@ __global__ void __launch_bounds__(NT) k_lwin(Group g, LwinCfg lc, const u32* occ
                                              const u32* occT, u16* cout, u8* lflag) {
   namespace cg = cooperative_groups;
   constexpr u32 WPT = (256 + NT - 1) / NT;  // occupancy words staged per thread
-  __shared__ u64 Qk[C][NT];      // suffix minimum at element e of chunk t: [e][t]
+  __shared__ u64 Qk[C][NT];      // in-chunk suffix minimum at element e of chunk t: [e][t]
   __shared__ u16 Qp[C][NT];      // its candidate's position on the line
+  __shared__ u64 Ek[NT];         // suffix minimum of the chunks after chunk t in its k-block
+  __shared__ u16 Ep[NT];
   __shared__ u32 w[256 + 2];     // staged occupancy words
   __shared__ u32 nw[256 + 2];    // first occupied position at / after word i
   __shared__ u32 wmin[NT / 32];
@@ -183,63 +185,75 @@ __global__ void __launch_bounds__(NT) k_lwin(Group g, LwinCfg lc, const u32* occ
     const u32 wdd = w[wi], nxtw = nw[wi + 1];
     const int e_lo = wdd ? (int)(31 - __clz(wdd)) - (int)rb + 1 : 0;
     const int e_hi = nxtw == LW_INF ? C : (int)nxtw - (int)k - (int)q0;
-    u64 agg = KEY_NONE;
-    u32 aggp = LW_SENT;
+    // the chunk's suffix minima, last element first; the one at element 0
+    // is the chunk minimum
+    u64 rk = KEY_NONE;
+    u32 rq = LW_SENT;
     if (e_lo <= e_hi && e_lo < C && e_hi >= 0) {
       any = true;
       const u64 zstep = F == 0 ? SM_GAMMA : SM_GAMMA * (u64)L;
       u64 z = g.base[s] + SM_GAMMA +
-              SM_GAMMA * (F == 0 ? (u64)line * L + xs : g.LL + (u64)xs * L + line);
+              SM_GAMMA * (F == 0 ? (u64)line * L + xs + C - 1 : g.LL + (u64)(xs + C - 1) * L + line);
 #pragma unroll
-      for (int e = 0; e < C; ++e, z += zstep) {
+      for (int e = C - 1; e >= 0; --e, z -= zstep) {
         const u64 h = mix64(z);
         v[e] = (e >= e_lo && e <= e_hi) ? h : KEY_NONE;
-        kp_min(agg, aggp, v[e], xs + e);
+        kp_min(rk, rq, v[e], xs + e);
+        Qk[e][tid] = rk;
+        Qp[e][tid] = (u16)rq;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < C; ++e) {
+        Qk[e][tid] = KEY_NONE;
+        Qp[e][tid] = (u16)LW_SENT;
       }
     }
     // chunk minima combined within each k-block (m consecutive chunks)
-    lw_block_scans(agg, aggp, m, ep, epp, es, esp, wtf, wtfp, wtb, wtbp);
-  }
-  // suffix minima within the k-block into shared memory (a span without
-  // live anchors publishes "none", so readers need not know)
-  {
-    u64 rk = es;
-    u32 rq = esp;
+    lw_block_scans(rk, rq, m, ep, epp, es, esp, wtf, wtfp, wtb, wtbp);
+  } else {
+    // a span without live anchors publishes "none", so readers need not know
 #pragma unroll
-    for (int e = C - 1; e >= 0; --e) {
-      kp_min(rk, rq, v[e], xs + e);
-      Qk[e][tid] = rk;
-      Qp[e][tid] = (u16)rq;
+    for (int e = 0; e < C; ++e) {
+      Qk[e][tid] = KEY_NONE;
+      Qp[e][tid] = (u16)LW_SENT;
     }
   }
+  Ek[tid] = es;
+  Ep[tid] = (u16)esp;
   cl.sync();  // suffix minima of every span of the line are in shared memory
   if (!(own_dead && prev_dead)) {
-    // cell q0 + e needs the suffix minimum at q0 + e - k + 1: element
-    // (e + 1) % C of chunk tid - m + (e + 1) / C, in the previous span when
-    // that chunk index is negative
-    const int cb = (int)tid - (int)m;
-    const u64* QkR = rp == r ? &Qk[0][0] : cl.map_shared_rank(&Qk[0][0], rp);
-    const u16* QpR = rp == r ? &Qp[0][0] : cl.map_shared_rank(&Qp[0][0], rp);
-    const int ca = cb, cc = cb + 1;
-    const u64* ka = ca >= 0 ? &Qk[0][ca] : QkR + (ca + (int)NT);
-    const u16* pa = ca >= 0 ? &Qp[0][ca] : QpR + (ca + (int)NT);
-    const u64* kc = cc >= 0 ? &Qk[0][cc] : QkR + (cc + (int)NT);
-    const u16* pc = cc >= 0 ? &Qp[0][cc] : QpR + (cc + (int)NT);
-    const bool closes = tid % m == m - 1;  // the chunk's last cell ends its k-block
-    u64 rk = ep;
-    u32 rq = epp;
+    // cell q0 + e needs the suffix minimum of its window's first k-block
+    // from q0 + e - k + 1 on, in chunk ca = tid - m (the previous span's
+    // chunk ca + NT when ca < 0): for e < C - 1 the smaller of ca's in-chunk
+    // suffix minimum at element e + 1 and the minimum E of the chunks after
+    // ca in that k-block; for e = C - 1 it is E alone (the chunk after ca,
+    // or nothing when this chunk ends its k-block, and then E is "none").
+    // E is folded into the running prefix minimum once.
+    const int ca = (int)tid - (int)m;
+    const u64* ka;
+    const u16* pa;
+    u64 rk;
+    u32 rq;
+    if (ca >= 0) {
+      ka = &Qk[0][ca];
+      pa = &Qp[0][ca];
+      rk = Ek[ca];
+      rq = Ep[ca];
+    } else {
+      ka = cl.map_shared_rank(&Qk[0][0], rp) + (ca + (int)NT);
+      pa = cl.map_shared_rank(&Qp[0][0], rp) + (ca + (int)NT);
+      rk = cl.map_shared_rank(&Ek[0], rp)[ca + (int)NT];
+      rq = cl.map_shared_rank(&Ep[0], rp)[ca + (int)NT];
+    }
+    kp_min(rk, rq, ep, epp);
     u32 packed[(C + 1) / 2];
 #pragma unroll
     for (int e = 0; e < C; ++e) {
-      kp_min(rk, rq, v[e], xs + e);  // prefix minimum within the k-block
+      kp_min(rk, rq, v[e], xs + e);  // prefix minimum within the k-block (and E)
       u64 mk = rk;
       u32 mq = rq;
-      const int el = (e + 1) % C;
-      if (e < C - 1) {
-        kp_min(mk, mq, ka[el * NT], pa[el * NT]);
-      } else if (!closes) {
-        kp_min(mk, mq, kc[0], pc[0]);
-      }
+      if (e < C - 1) kp_min(mk, mq, ka[(e + 1) * NT], pa[(e + 1) * NT]);
       const u32 x = xs + e;
       u32 d = x - mq;
       if (x < mq) d += L;
@@ -288,21 +302,35 @@ struct AccMasks {
 // accepted iff it is the smallest live candidate on each of its k cells, and
 // since the winners' anchors are monotone along a line that holds iff cell
 // a has it as winner at offset 0, cell a + k - 1 at offset k - 1, and every
-// cell in between is won by its orientation (k_lacc).  One warp per strip of
-// 32 columns x 16 rows, all its global loads issued first: lane = column,
-// walking down it (vertical winners' priorities and offsets, kept in shared
-// memory), then lane = (row, half-row), walking along it (horizontal
-// winners, compared with the vertical ones; row masks), then lane = column
-// again for the column masks.  A winner's priority is recomputed only when
-// its anchor changes along the walk.  cdead[s * 2 T^2 + strip] is set once
-// no cell of the strip is covered by a live candidate (it stays so, with
-// its masks zero; later rounds skip it).
-constexpr u32 LC_WARPS = 8;
+// cell in between is won by its orientation (k_lacc).  One warp per square
+// of 32 x 32 cells, all its global loads (64 bytes of offsets per lane and
+// orientation) issued first: lane = column, walking down it (the vertical
+// winners' priorities go to shared memory; bits of the cells whose vertical
+// offset is 0 or k - 1), then lane = row, walking along it (horizontal
+// winners compared with the vertical ones: the row masks, and a bit per cell
+// that the vertical candidate wins); a 32 x 32 bit transpose across the warp
+// turns those bits into the column masks.  A winner's priority is recomputed
+// only when its anchor changes along the walk.  cdead[s * T^2 + square] is
+// set once no cell of the square is covered by a live candidate (it stays
+// so, with its masks zero; later rounds skip it).
+constexpr u32 LC_WARPS = 4;
 struct LcombSmem {
-  u64 vk[LC_WARPS][32][17];   // vertical winners' priorities [x][y]
-  u16 vd[LC_WARPS][32][18];   // their offsets [x][y]
-  u16 cs[LC_WARPS][16][34];   // final codes [y][x]: d, CODE_V | d or CODE_NONE
+  u64 vk[LC_WARPS][32][33];   // vertical winners' priorities [x][y]
 };
+
+// 32 x 32 bit-matrix transpose across a warp: lane r holds row r (bit c is
+// entry (r, c)); on return lane c holds column c (bit r is entry (r, c)).
+// Step j swaps the off-diagonal j x j blocks of every 2j x 2j block.
+__device__ __forceinline__ u32 warp_transpose32(u32 x, u32 lane) {
+  constexpr u32 lo[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const u32 j = 16u >> i, m = lo[i];
+    const u32 t = __shfl_xor_sync(FULL, x, j);
+    x = (lane & j) ? ((x & ~m) | ((t >> j) & m)) : ((x & m) | ((t << j) & ~m));
+  }
+  return x;
+}
 
 __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH, const u16* cV,
                                                          AccMasks mh, AccMasks mv, u8* cdead) {
@@ -310,33 +338,38 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
   LcombSmem& sm = *reinterpret_cast<LcombSmem*>(smem_raw);
   const u32 s = blockIdx.y;
   if (g.st[s].done) return;
-  const u32 L = g.L, k = g.k, T = L / 32, NS = 2 * T * T;  // strips per sample
+  const u32 L = g.L, k = g.k, T = L / 32, NQ = T * T;  // squares per sample
   const u32 lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const u32 strip = blockIdx.x * LC_WARPS + wp;
-  if (strip >= NS) return;
-  u8* dflag = cdead + (size_t)s * NS + strip;
+  const u32 sq = blockIdx.x * LC_WARPS + wp;
+  if (sq >= NQ) return;
+  u8* dflag = cdead + (size_t)s * NQ + sq;
   if (*dflag) return;
-  const u32 sy = strip / T, tx = strip - sy * T, Y = sy * 16, X = tx * 32;
+  const u32 ty = sq / T, tx = sq - ty * T, Y = ty * 32, X = tx * 32;
   const u64 zb = g.base[s] + SM_GAMMA;
   const size_t so = (size_t)s * g.LL;
-  u64 (*vk)[17] = sm.vk[wp];
-  u16 (*vd)[18] = sm.vd[wp];
-  u16 (*cs)[34] = sm.cs[wp];
-  const u32 row = lane & 15, half = lane >> 4;
-  // vertical offsets of column X + lane (rows Y .. Y + 15), horizontal
-  // offsets of row Y + row (columns X + 16 half ..): 32 bytes each
+  u64 (*vk)[33] = sm.vk[wp];
+  // vertical offsets of column X + lane (rows Y .. Y + 31), horizontal
+  // offsets of row Y + lane (columns X .. X + 31)
   const uint4* vsrc = reinterpret_cast<const uint4*>(cV + so + (size_t)(X + lane) * L + Y);
-  const uint4* hsrc = reinterpret_cast<const uint4*>(cH + so + (size_t)(Y + row) * L + X + 16 * half);
-  const uint4 v0 = __ldg(vsrc), v1 = __ldg(vsrc + 1);
-  const uint4 h0 = __ldg(hsrc), h1 = __ldg(hsrc + 1);
-  const u32 cvw[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-  const u32 chw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+  const uint4* hsrc = reinterpret_cast<const uint4*>(cH + so + (size_t)(Y + lane) * L + X);
+  u32 cvw[16], chw[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint4 a = __ldg(vsrc + i);
+    cvw[4 * i] = a.x, cvw[4 * i + 1] = a.y, cvw[4 * i + 2] = a.z, cvw[4 * i + 3] = a.w;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint4 a = __ldg(hsrc + i);
+    chw[4 * i] = a.x, chw[4 * i + 1] = a.y, chw[4 * i + 2] = a.z, chw[4 * i + 3] = a.w;
+  }
+  u32 v0 = 0, vl = 0;  // rows of column X + lane with vertical offset 0, k - 1
   {
     const u32 x = X + lane;
     u32 ca = NONE32;
     u64 ck = KEY_NONE;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {
       const u32 d = (cvw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
       const bool has = d != CODE_NONE;
       u32 ya = Y + i + L - d;
@@ -347,69 +380,46 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
         ca = ya;
       }
       vk[lane][i] = has ? ck : KEY_NONE;
-      vd[lane][i] = (u16)d;
+      v0 |= (u32)(d == 0) << i;
+      vl |= (u32)(d == k - 1) << i;
     }
   }
   __syncwarp();
-  bool any = false;
+  u32 bw = 0, b0 = 0, bk = 0, bv = 0;  // row masks; bv: cells the vertical winner takes
   {
-    const u32 y = Y + row, xb = 16 * half;
+    const u32 y = Y + lane;
     u32 ca = NONE32;
     u64 ck = KEY_NONE;
-    u32 bw = 0, b0 = 0, bk = 0;  // row mask bits of this half-row
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {
       const u32 d = (chw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
       const bool has = d != CODE_NONE;
-      u32 xa = X + xb + i + L - d;
+      u32 xa = X + i + L - d;
       if (xa >= L) xa -= L;
       if (has && xa != ca) {
         ck = mix64(zb + SM_GAMMA * ((u64)y * L + xa));
         ca = xa;
       }
       const u64 kh = has ? ck : KEY_NONE;
-      const u64 kv = vk[xb + i][row];
-      const u32 dv = CODE_V | vd[xb + i][row];
+      const u64 kv = vk[i][lane];
       const bool hw = kh < kv;
-      const u32 cd = hw ? d : (kv < kh ? dv : (u32)CODE_NONE);
-      any |= cd != CODE_NONE;
-      cs[row][xb + i] = (u16)cd;
       bw |= (u32)hw << i;
+      bv |= (u32)(kv < kh) << i;
       b0 |= (u32)(hw && d == 0) << i;
       bk |= (u32)(hw && d == k - 1) << i;
     }
-    // the two halves of a row make one mask word
-    bw |= __shfl_down_sync(FULL, bw, 16) << 16;
-    b0 |= __shfl_down_sync(FULL, b0, 16) << 16;
-    bk |= __shfl_down_sync(FULL, bk, 16) << 16;
-    if (half == 0) {
-      const size_t wi = ((size_t)s * L + y) * T + tx;
-      mh.win[wi] = bw;
-      mh.first[wi] = b0;
-      mh.last[wi] = bk;
-    }
   }
-  __syncwarp();
-  {
-    // column masks: bits Y .. Y + 15 of column X + lane, half a word of
-    // the transposed layout
-    u32 bw = 0, b0 = 0, bk = 0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const u32 cd = cs[i][lane];
-      const bool vw = cd != CODE_NONE && (cd & CODE_V);
-      const u32 dv = cd & ~(u32)CODE_V;
-      bw |= (u32)vw << i;
-      b0 |= (u32)(vw && dv == 0) << i;
-      bk |= (u32)(vw && dv == k - 1) << i;
-    }
-    const size_t hi = (((size_t)s * L + X + lane) * T + (Y >> 5)) * 2 + ((Y >> 4) & 1);
-    reinterpret_cast<u16*>(mv.win)[hi] = (u16)bw;
-    reinterpret_cast<u16*>(mv.first)[hi] = (u16)b0;
-    reinterpret_cast<u16*>(mv.last)[hi] = (u16)bk;
-  }
-  if (lane == 0) work_add(g, 3, 512);
-  if (!__any_sync(FULL, any) && lane == 0) *dflag = 1;
+  const size_t wi = ((size_t)s * L + Y + lane) * T + tx;
+  mh.win[wi] = bw;
+  mh.first[wi] = b0;
+  mh.last[wi] = bk;
+  const u32 cw = warp_transpose32(bv, lane);  // bit i: cell (Y + i, X + lane)
+  const size_t wj = ((size_t)s * L + X + lane) * T + ty;
+  mv.win[wj] = cw;
+  mv.first[wj] = cw & v0;
+  mv.last[wj] = cw & vl;
+  if (lane == 0) work_add(g, 3, 1024);
+  if (!__any_sync(FULL, (bw | bv) != 0) && lane == 0) *dflag = 1;
 }
 
 // Record accepted candidate `idx` (anchor at position `pos` of line `line`,

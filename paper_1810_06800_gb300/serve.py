@@ -3,10 +3,11 @@
 A job asks for ``n`` samples of an (L, k) lattice with seeds seed .. seed+n-1.
 Jobs are split into batches; a batch is admitted as soon as its device
 workspace (``rsa_workspace_bytes``) fits in the free-HBM budget and a worker
-is idle.  Workers are host threads, each with its own CUDA stream and its
-own handles (one per lattice shape); the library call releases the GIL, so
-batches of different jobs run on the GPU at the same time and jobs that
-arrive while others run are admitted as memory and workers free up.  The
+is idle, the job that has received the least service so far first.  Workers
+are host threads, each with its own CUDA stream and its own handles (one
+per lattice shape); the library call releases the GIL, so batches of
+different jobs run on the GPU at the same time and jobs that arrive while
+others run are admitted as memory and workers free up.  The
 per-batch workspace is a torch tensor bound to the handle, returned to
 torch's caching allocator when the batch ends, so lattice state stays on the
 device and nothing is copied back but n_j and n_c.
@@ -52,6 +53,7 @@ class Job:
     t_start: float = None  # its first batch started on a worker
     error: str = None
     cancelled: bool = False
+    attained: int = 0      # lattice sites of its batches started so far
     from_journal: int = 0  # samples filled from the journal
     done_event: threading.Event = field(default_factory=threading.Event)
 
@@ -182,27 +184,38 @@ class Scheduler:
             self.cv.notify_all()
 
     def _take(self):
-        """Next batch to run: the oldest pending batch if it fits the free
-        budget; otherwise the oldest later batch that fits (first fit), unless
-        the head has already waited max_wait_s, in which case nothing
-        overtakes it until memory frees up for it."""
+        """Next batch to run.  Among the jobs with a pending batch, the one
+        that has received the least service so far (lattice sites of its
+        batches already started) goes first, then the earliest arrival: a
+        short job that arrives behind a long one waits for a worker to finish
+        one batch, not for the long job, and jobs of equal service take turns.
+        A batch runs only if its workspace fits the free budget.  The oldest
+        job's next batch, once it has waited max_wait_s without fitting, is
+        not overtaken until memory frees up for it."""
         with self.cv:
             while True:
                 if self.closed and not self.pending:
                     return None
                 pick = None
                 if self.pending:
+                    heads = {}  # job -> index of its next batch (pending is in submit order)
+                    for i, b in enumerate(self.pending):
+                        heads.setdefault(id(b.job), i)
                     head = self.pending[0]
-                    if self.in_flight_bytes + head.bytes <= self.budget:
-                        pick = 0
-                    elif self.clock() - head.job.t_arrival < self.max_wait_s:
-                        for i in range(1, len(self.pending)):
-                            if self.in_flight_bytes + self.pending[i].bytes <= self.budget:
-                                pick = i
-                                break
+                    if (self.in_flight_bytes + head.bytes > self.budget
+                            and self.clock() - head.job.t_arrival >= self.max_wait_s):
+                        order = [0]
+                    else:
+                        order = sorted(heads.values(),
+                                       key=lambda i: (self.pending[i].job.attained, i))
+                    for i in order:
+                        if self.in_flight_bytes + self.pending[i].bytes <= self.budget:
+                            pick = i
+                            break
                 if pick is not None:
                     b = self.pending[pick]
                     del self.pending[pick]
+                    b.job.attained += b.job.L * b.job.L * b.n
                     self.in_flight_bytes += b.bytes
                     self.running += 1
                     self.peak_bytes = max(self.peak_bytes, self.in_flight_bytes)
@@ -314,11 +327,17 @@ class GpuRunner:
             for h in hs.values():
                 self.rsa.rsa_destroy(h)
             hs.clear()
+        for st in self.streams:
+            st.synchronize()
+        self.torch.cuda.empty_cache()
 
 
 def gpu_budget(reserve_frac: float = 0.1, device: int = 0) -> int:
-    """Free HBM now, less a reserve for torch, the library and other users."""
+    """Free HBM now, less a reserve for torch, the library and other users.
+    Blocks that torch's caching allocator holds but no tensor uses (an earlier
+    server's workspaces) are returned to the device first."""
     import torch
+    torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info(device)
     return int(free - reserve_frac * total)
 

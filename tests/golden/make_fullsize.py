@@ -2,8 +2,8 @@
 """Write tests/golden/fullsize.json: oracle results of full-size samples.
 
 The oracle (a sequential priority-order scan plus union-find, Sec. II.B to
-II.D of arXiv:1810.06800) needs minutes per sample at L = 8192 and about half
-an hour and 53 GB of host memory per sample at L = 32768, too long to rerun
+II.D of arXiv:1810.06800) needs minutes per sample at L = 8192 and over an
+hour and 35 GB of host memory per sample at L = 32768, too long to rerun
 inside a test.  This script runs it once, one sample at a time, and stores
 per (L, k, seed):
   n_j       number of accepted k-mers at jamming,

@@ -1,6 +1,7 @@
 """Continuous-batching scheduler (host logic on CPU with a fake runner) and
 the served path on the GPU: every job's results are identical alone and in
 a mix, and match the oracle."""
+import itertools
 import threading
 import time
 
@@ -198,3 +199,38 @@ def test_served_large_k_jobs_alone_and_in_a_mix_match():
         if j.L <= 1024:
             wj, wc = oracle.samples(j.L, j.k, list(range(j.seed, j.seed + j.n)))
             assert np.array_equal(j.nj, wj.astype(np.uint32)) and np.array_equal(j.nc, wc.astype(np.uint32))
+
+
+def test_short_job_does_not_wait_behind_a_long_one():
+    # one worker; a 20-batch job arrives first, a one-batch job just after:
+    # the short job runs after at most two of the long job's batches
+    log, lock = [], threading.Lock()
+    sch = serve.Scheduler(_fake_runner(log, lock, delay=0.02), _fake_ws, 10**9, workers=1,
+                          max_batch=2)
+    long_job = sch.submit(serve.Job(0, 64, 4, 40, 1))
+    short = sch.submit(serve.Job(1, 32, 2, 2, 50))
+    assert short.done_event.wait(10) and long_job.done_event.wait(10)
+    sch.close()
+    starts = [b for ev, _, b in log if ev == "start"]
+    assert starts.index(32 * 32 * 2) <= 2
+    assert short.t_done < long_job.t_done
+    wj, wc = _expected(32, 2, 50, 2)
+    assert np.array_equal(short.nj, wj) and np.array_equal(short.nc, wc)
+    wj, wc = _expected(64, 4, 1, 40)
+    assert np.array_equal(long_job.nj, wj) and np.array_equal(long_job.nc, wc)
+
+
+def test_jobs_of_equal_service_take_turns():
+    # two equal jobs on one worker alternate batch by batch
+    log, lock = [], threading.Lock()
+    sch = serve.Scheduler(_fake_runner(log, lock, delay=0.005), _fake_ws, 10**9, workers=1,
+                          max_batch=1)
+    a = sch.submit(serve.Job(0, 16, 2, 6, 1))
+    b = sch.submit(serve.Job(1, 17, 2, 6, 1))
+    assert a.done_event.wait(10) and b.done_event.wait(10)
+    sch.close()
+    sizes = [n for ev, _, n in log if ev == "start"]
+    # after the first batch (taken before job b existed, or a's by arrival)
+    # neither job runs three batches in a row
+    runs = max(len(list(g)) for _, g in itertools.groupby(sizes))
+    assert runs <= 2
