@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 
 #include "rsa_line.cuh"
+#include "rsa_tile.cuh"  // cp.async helpers
 
 namespace rsak {
 
@@ -303,19 +304,32 @@ struct AccMasks {
 // since the winners' anchors are monotone along a line that holds iff cell
 // a has it as winner at offset 0, cell a + k - 1 at offset k - 1, and every
 // cell in between is won by its orientation (k_lacc).  One warp per square
-// of 32 x 32 cells, all its global loads (64 bytes of offsets per lane and
-// orientation) issued first: lane = column, walking down it (the vertical
-// winners' priorities go to shared memory; bits of the cells whose vertical
-// offset is 0 or k - 1), then lane = row, walking along it (horizontal
-// winners compared with the vertical ones: the row masks, and a bit per cell
-// that the vertical candidate wins); a 32 x 32 bit transpose across the warp
-// turns those bits into the column masks.  A winner's priority is recomputed
-// only when its anchor changes along the walk.  cdead[s * T^2 + square] is
-// set once no cell of the square is covered by a live candidate (it stays
-// so, with its masks zero; later rounds skip it).
+// of 32 x 32 cells, all its loads (the offsets of both orientations, 4 KB,
+// coalesced into shared memory) issued first: lane = column, walking down it (the vertical
+// winners' offsets and the high 32 bits of their priorities go to shared
+// memory; bits of the cells whose vertical offset is 0 or k - 1), then lane
+// = row, walking along it (horizontal winners compared with the vertical
+// ones: the row masks, and a bit per cell that the vertical candidate wins);
+// a 32 x 32 bit transpose across the warp turns those bits into the column
+// masks.  Two priorities with equal high halves (rare) are compared in full,
+// the vertical one recomputed from its offset.  A winner's priority is
+// recomputed only when its anchor changes along the walk; the hash is an
+// out-of-line call so that the fully unrolled walks stay small.
+// cdead[s * T^2 + square] is set once no cell of the square is covered by a
+// live candidate (it stays so, with its masks zero; later rounds skip it).
 constexpr u32 LC_WARPS = 4;
+union LcombWarp {
+  // the square's offsets as loaded: [orientation][line][16 words], the four
+  // 16-byte chunks of line r stored in the order c ^ ((r >> 1) & 3), so that
+  // both the coalesced stores and the per-line reads are conflict-free
+  u32 stage[2][32][16];
+  struct {
+    u32 vh[32][33];   // high halves of the vertical winners' priorities [x][y]
+    u16 vd[32][34];   // their offsets [x][y], CODE_NONE if none
+  } w;
+};
 struct LcombSmem {
-  u64 vk[LC_WARPS][32][33];   // vertical winners' priorities [x][y]
+  LcombWarp wp[LC_WARPS];
 };
 
 // 32 x 32 bit-matrix transpose across a warp: lane r holds row r (bit c is
@@ -332,7 +346,9 @@ __device__ __forceinline__ u32 warp_transpose32(u32 x, u32 lane) {
   return x;
 }
 
-__global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH, const u16* cV,
+__device__ __noinline__ u64 mix64_call(u64 z) { return mix64(z); }
+
+__global__ void __launch_bounds__(LC_WARPS * 32, 8) k_lcomb(Group g, const u16* cH, const u16* cV,
                                                          AccMasks mh, AccMasks mv, u8* cdead) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   LcombSmem& sm = *reinterpret_cast<LcombSmem*>(smem_raw);
@@ -347,27 +363,36 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
   const u32 ty = sq / T, tx = sq - ty * T, Y = ty * 32, X = tx * 32;
   const u64 zb = g.base[s] + SM_GAMMA;
   const size_t so = (size_t)s * g.LL;
-  u64 (*vk)[33] = sm.vk[wp];
-  // vertical offsets of column X + lane (rows Y .. Y + 31), horizontal
-  // offsets of row Y + lane (columns X .. X + 31)
-  const uint4* vsrc = reinterpret_cast<const uint4*>(cV + so + (size_t)(X + lane) * L + Y);
-  const uint4* hsrc = reinterpret_cast<const uint4*>(cH + so + (size_t)(Y + lane) * L + X);
+  LcombWarp& ws = sm.wp[wp];
+  u32 (*vh)[33] = ws.w.vh;
+  u16 (*vd)[34] = ws.w.vd;
+  // the square's 64-byte line pieces, four lanes per line (coalesced), into
+  // shared memory: vertical offsets of columns X .. X + 31 (rows Y ..
+  // Y + 31), horizontal offsets of rows Y .. Y + 31 (columns X .. X + 31)
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const u32 r = 8 * j + (lane >> 2), c = lane & 3, cs = c ^ ((r >> 1) & 3u);
+    cp_async16(&ws.stage[0][r][cs * 4], cV + so + (size_t)(X + r) * L + Y + c * 8);
+    cp_async16(&ws.stage[1][r][cs * 4], cH + so + (size_t)(Y + r) * L + X + c * 8);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  // lane = line: column X + lane's vertical and row Y + lane's horizontal
+  // offsets, 16 words each
   u32 cvw[16], chw[16];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint4 a = __ldg(vsrc + i);
-    cvw[4 * i] = a.x, cvw[4 * i + 1] = a.y, cvw[4 * i + 2] = a.z, cvw[4 * i + 3] = a.w;
+  for (int j = 0; j < 4; ++j) {
+    const u32 cs = (u32)j ^ ((lane >> 1) & 3u);
+    const uint4 a = *reinterpret_cast<const uint4*>(&ws.stage[0][lane][cs * 4]);
+    const uint4 b = *reinterpret_cast<const uint4*>(&ws.stage[1][lane][cs * 4]);
+    cvw[4 * j] = a.x, cvw[4 * j + 1] = a.y, cvw[4 * j + 2] = a.z, cvw[4 * j + 3] = a.w;
+    chw[4 * j] = b.x, chw[4 * j + 1] = b.y, chw[4 * j + 2] = b.z, chw[4 * j + 3] = b.w;
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint4 a = __ldg(hsrc + i);
-    chw[4 * i] = a.x, chw[4 * i + 1] = a.y, chw[4 * i + 2] = a.z, chw[4 * i + 3] = a.w;
-  }
+  __syncwarp();  // the staging area is reused for the vertical winners
   u32 v0 = 0, vl = 0;  // rows of column X + lane with vertical offset 0, k - 1
   {
     const u32 x = X + lane;
-    u32 ca = NONE32;
-    u64 ck = KEY_NONE;
+    u32 ca = NONE32, ch = 0;
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
       const u32 d = (cvw[i >> 1] >> ((i & 1) * 16)) & 0xFFFFu;
@@ -376,10 +401,11 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
       if (ya >= L) ya -= L;
       // the only branch: a new anchor along the column
       if (has && ya != ca) {
-        ck = mix64(zb + SM_GAMMA * (g.LL + (u64)ya * L + x));
+        ch = (u32)(mix64_call(zb + SM_GAMMA * (g.LL + (u64)ya * L + x)) >> 32);
         ca = ya;
       }
-      vk[lane][i] = has ? ck : KEY_NONE;
+      vh[lane][i] = ch;
+      vd[lane][i] = (u16)d;
       v0 |= (u32)(d == 0) << i;
       vl |= (u32)(d == k - 1) << i;
     }
@@ -397,14 +423,26 @@ __global__ void __launch_bounds__(LC_WARPS * 32) k_lcomb(Group g, const u16* cH,
       u32 xa = X + i + L - d;
       if (xa >= L) xa -= L;
       if (has && xa != ca) {
-        ck = mix64(zb + SM_GAMMA * ((u64)y * L + xa));
+        ck = mix64_call(zb + SM_GAMMA * ((u64)y * L + xa));
         ca = xa;
       }
-      const u64 kh = has ? ck : KEY_NONE;
-      const u64 kv = vk[i][lane];
-      const bool hw = kh < kv;
+      const u32 dv = vd[i][lane];
+      const bool hasv = dv != CODE_NONE;
+      const u32 khi = (u32)(ck >> 32), kvhi = vh[i][lane];
+      bool hw, vw;
+      if (has && hasv && khi == kvhi) {
+        // equal high halves: compare the full priorities
+        u32 ya = y + L - dv;
+        if (ya >= L) ya -= L;
+        const u64 kv = mix64_call(zb + SM_GAMMA * (g.LL + (u64)ya * L + X + i));
+        hw = ck < kv;
+        vw = kv < ck;
+      } else {
+        hw = has && (!hasv || khi < kvhi);
+        vw = hasv && (!has || kvhi < khi);
+      }
       bw |= (u32)hw << i;
-      bv |= (u32)(kv < kh) << i;
+      bv |= (u32)vw << i;
       b0 |= (u32)(hw && d == 0) << i;
       bk |= (u32)(hw && d == k - 1) << i;
     }
