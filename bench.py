@@ -448,6 +448,7 @@ def run_mix(args, groups, world, rank, local):
     # ---- device-timed: events on the caller's stream bracket every call
     clocks = ClockSampler(local)
     barrier()
+    rsa.rsa_mix_launches()   # reset the launch count
     clocks.start()
     time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -461,6 +462,7 @@ def run_mix(args, groups, world, rank, local):
     wall = time.perf_counter() - t0
     barrier()
     ck = clocks.stop()
+    gpu_launches = rsa.rsa_mix_launches()   # kernels of the timed calls
     ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
     wall = max_over_ranks(wall, pg, "cuda")
     assert np.array_equal(nj, nj2) and np.array_equal(nc, nc2)
@@ -529,7 +531,7 @@ def run_mix(args, groups, world, rank, local):
                 "d2h_bytes_per_step": 8 * n},
         "plain_per_shape_handles": {"value": plain, "unit": "samples/s",
                                     "per_shape": per_shape},
-        "gpu_launches": None,
+        "gpu_launches": gpu_launches,
         "roofline": roof,
         "kernels": {nm: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / total, 4)}
                     for nm, v in kst.items()},

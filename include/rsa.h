@@ -120,6 +120,10 @@ int rsa_run_small(const uint32_t *L, const uint32_t *k, const uint64_t *seeds, u
 int rsa_run_mix(const uint32_t *L, const uint32_t *k, const uint64_t *seeds, uint32_t n,
                 uint32_t *n_j, uint32_t *n_c, void *stream);
 void rsa_mix_release(void);
+/* Measurement support (no counterpart in the paper): the number of kernel
+ * launches made by rsa_run_small and by rsa_run_mix's cached handles since
+ * the previous call, then reset.  Synchronises those handles' streams. */
+unsigned long long rsa_mix_launches(void);
 
 /* How a shape runs: RSA_MODE_SMALL (one CTA per sample, `threads` per CTA)
  * or RSA_MODE_GLOBAL (the tiled / long-k / general kernels over the whole

@@ -16,6 +16,7 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdio>
 #include <cstdlib>
@@ -58,6 +59,9 @@ int status_to_code(u32 bits) {
   if (bits & ST_NODE_OVF) return RSA_ENOMEM;
   return 0;
 }
+
+// k_small launches since the last rsa_mix_launches() call.
+std::atomic<unsigned long long> g_small_launches{0};
 
 // Resident CTAs of k_small per SM for a CTA size and lattice bound.
 int small_blocks_per_sm(uint32_t threads, uint32_t Lm, int* out) {
@@ -110,6 +114,7 @@ extern "C" int rsa_run_small(const uint32_t* L, const uint32_t* k, const uint64_
     const u32 grid = (u32)std::min<uint64_t>(n, (uint64_t)sms * bps);
     k_small<<<grid, threads, small_smem_bytes(Lm), st>>>(djobs, n, dout, dnext, Lm, UF_CAP);
     e = cudaGetLastError();
+    if (e == cudaSuccess) g_small_launches.fetch_add(1);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), dout, ob, cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(d, st);
@@ -492,6 +497,22 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
   for (auto& e : errs)
     if (e.first) return set_error(e.first, e.second);
   return 0;
+}
+
+extern "C" unsigned long long rsa_mix_launches(void) {
+  unsigned long long total = g_small_launches.exchange(0);
+  uint32_t nk = 0;
+  while (rsa_kernel_name(nk)[0]) ++nk;
+  std::vector<double> ms(nk);
+  std::vector<unsigned long long> ln(nk);
+  std::lock_guard<std::mutex> lock(g_mix_mu);
+  for (auto& kv : g_mix) {
+    std::lock_guard<std::mutex> slot_lock(kv.second->mu);
+    if (!kv.second->h) continue;
+    if (rsa_kernel_stats(kv.second->h, ms.data(), ln.data(), nk) == 0)
+      for (unsigned long long v : ln) total += v;
+  }
+  return total;
 }
 
 extern "C" void rsa_mix_release(void) {

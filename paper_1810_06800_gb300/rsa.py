@@ -25,7 +25,7 @@ SYMBOLS = ["rsa_create", "rsa_run_batch", "rsa_run_seeds", "rsa_run_keys", "rsa_
            "rsa_workspace_bytes", "rsa_bind_workspace", "rsa_test_caps",
            "rsa_run_small", "rsa_run_mix", "rsa_tune", "rsa_set_rounds_per_check",
            "rsa_set_window_threads",
-           "rsa_mix_release", "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
+           "rsa_mix_release", "rsa_mix_launches", "rsa_profile", "rsa_kernel_stats", "rsa_work_stats", "rsa_destroy", "rsa_kernel_name",
            "rsa_last_error"]
 
 _lib = None
@@ -81,6 +81,7 @@ def load():
     lib.rsa_set_rounds_per_check.argtypes = [vp, u32]
     lib.rsa_set_window_threads.argtypes = [vp, u32]
     lib.rsa_mix_release.argtypes = []
+    lib.rsa_mix_launches.argtypes = []
     lib.rsa_destroy.argtypes = [vp]
     lib.rsa_destroy.restype = None
     lib.rsa_profile.argtypes = [vp, ip]
@@ -93,6 +94,7 @@ def load():
     for name in SYMBOLS[:-3]:
         getattr(lib, name).restype = ip
     lib.rsa_mix_release.restype = None
+    lib.rsa_mix_launches.restype = ctypes.c_ulonglong
     _lib = lib
     return lib
 
@@ -179,6 +181,11 @@ def rsa_run_mix(L, k, seeds, stream=None):
 
 def rsa_mix_release():
     load().rsa_mix_release()
+
+
+def rsa_mix_launches() -> int:
+    """Kernel launches of rsa_run_small and rsa_run_mix since the last call."""
+    return int(load().rsa_mix_launches())
 
 
 def rsa_tune(L: int, k: int, n: int, measure: bool = True) -> dict:
