@@ -745,7 +745,10 @@ int run_impl(rsa_t* h, const uint64_t* seeds, u32 n, const uint64_t* keys, cudaS
   {
     // rows per sample spread over enough blocks to fill the GPU across the batch
     const u32 bx = (u32)std::min<u64>(h->L, std::max<u64>(1, 65536 / n));
-    launch(h, KD_EDGES, k_edges, dim3(bx, n), dim3(EDGES_THREADS), 0, stream, g);
+    if (h->L % 4 == 0 && h->L >= 8)
+      launch(h, KD_EDGES, k_edges4, dim3(bx, n), dim3(EDGES_THREADS), 0, stream, g);
+    else
+      launch(h, KD_EDGES, k_edges, dim3(bx, n), dim3(EDGES_THREADS), 0, stream, g);
     if ((rc = launch_check("k_edges"))) return rc;
   }
   launch(h, KD_BUCKET, k_bucket, dim3(n), dim3(1024), 0, stream, g);

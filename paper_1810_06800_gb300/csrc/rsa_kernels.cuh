@@ -237,6 +237,87 @@ __device__ __forceinline__ u32 contact_delta(const Group& g, u32 s, u32 y, u32 x
 
 constexpr u32 EDGES_THREADS = 256;
 
+// The two contacts (+x, +y) of cell (y, x) of owner a, given the owners of
+// its neighbours (right, down, up, up-right, left, down-left): counted by
+// class into cnt, and emitted as graph edges unless internal to one k-mer or
+// a repeat of the previous contact of their run.  Every lane of the warp
+// calls it (ballots inside); a lane with nothing to do passes a = NONE32.
+__device__ __forceinline__ void edge_cell(const Group& g, u32 s, SampleState& st, const u64* nkey,
+                                          Edge* E, bool full_compare, u32 lane, u32 y, u32 x,
+                                          u32 yp, u32 yn, u32 xp, u32 xn, u32 a, u32 o_r,
+                                          u32 o_d, u32 o_u, u32 o_ur, u32 o_l, u32 o_dl,
+                                          u32 cnt[3]) {
+#pragma unroll
+  for (u32 dir = 0; dir < 2; ++dir) {
+    const u32 by = dir ? yn : y, bx = dir ? x : xn;
+    bool emit = false;
+    u32 b = NONE32, d = 0;
+    u32 kind = 3;  // contact class: 0 both horizontal, 1 both vertical, 2 mixed
+    if (a != NONE32) {
+      b = dir ? o_d : o_r;
+      // owner words carry the k-mer's orientation in bit 31
+      if (b != NONE32 && b != a) kind = (a ^ b) >> 31 ? 2u : a >> 31;
+      if (b != NONE32) {
+        bool internal = false;
+        // the previous contact of the run: one row up (+x edges) or one
+        // column left (+y edges)
+        const bool force = dir == 0 ? (y == 0) : (x == 0);
+        const u32 py = dir == 0 ? yp : y, px = dir == 0 ? x : xp;
+        const u32 qy = dir == 0 ? yp : yn, qx = dir == 0 ? xn : xp;
+        const u32 pa = force ? NONE32 : (dir == 0 ? o_u : o_l);
+        const u32 pb = force ? NONE32 : (dir == 0 ? o_ur : o_dl);
+        const bool same_pair = pa == a && pb == b;
+        if (!same_pair || full_compare) {
+          d = contact_delta(g, s, y, x, by, bx, dir, a & ~OWN_V, b & ~OWN_V, &internal);
+          emit = !internal;
+          if (emit && same_pair) {
+            bool pint = false;
+            const u32 pd = contact_delta(g, s, py, px, qy, qx, dir, pa & ~OWN_V, pb & ~OWN_V,
+                                         &pint);
+            emit = pd != d;
+          }
+        }
+      }
+    }
+    // interspecific-contact counts (Sec. II.A): every contact, before the
+    // run deduplication of the graph edges
+    cnt[0] += kind == 0;
+    cnt[1] += kind == 1;
+    cnt[2] += kind == 2;
+    const u32 mask = __ballot_sync(FULL, emit);
+    if (!mask) continue;
+    u32 basei = 0;
+    const u32 leader = __ffs(mask) - 1;
+    if (lane == leader) basei = atomicAdd(&st.n_edges, (u32)__popc(mask));
+    basei = __shfl_sync(FULL, basei, leader);
+    if (emit) {
+      const u32 e = basei + __popc(mask & ((1u << lane) - 1u));
+      if (e < g.edge_limit) {
+        Edge ed;
+        const u32 ma = a & ~OWN_V, mb = b & ~OWN_V;
+        ed.time = max(nkey[ma], nkey[mb]);
+        ed.m1 = ma;
+        ed.m2 = mb;
+        ed.dxy = d;
+        ed.pad = 0;
+        E[e] = ed;
+      } else {
+        atomicOr(&st.status, ST_EDGE_OVF);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void edge_counts(SampleState& st, u32 lane, const u32 cnt[3]) {
+#pragma unroll
+  for (u32 c = 0; c < 3; ++c) {
+    const u32 t = __reduce_add_sync(FULL, cnt[c]);
+    if (lane == 0 && t)
+      atomicAdd(c == 0 ? &st.contacts_x : c == 1 ? &st.contacts_y : &st.contacts_xy, t);
+  }
+}
+
+// Any L: one cell per thread per step.
 __global__ void __launch_bounds__(EDGES_THREADS) k_edges(Group g) {
   const u32 s = blockIdx.y;
   const u32 L = g.L;
@@ -250,7 +331,7 @@ __global__ void __launch_bounds__(EDGES_THREADS) k_edges(Group g) {
   // their owners alone; rings (k = L) and tiny lattices compare displacements.
   const bool full_compare = g.k == L || L <= 2;
   // block b walks rows b, b + gridDim.x, ...; its threads stride along the
-  // row (every lane of a warp runs the same number of steps: ballots below)
+  // row (every lane of a warp runs the same number of steps: ballots inside)
   const u32 xsteps = (L + blockDim.x - 1) / blockDim.x;
   u32 cnt[3] = {0, 0, 0};
   for (u32 y = blockIdx.x; y < L; y += gridDim.x)
@@ -267,72 +348,53 @@ __global__ void __launch_bounds__(EDGES_THREADS) k_edges(Group g) {
     const u32 o_r = __ldg(own + (size_t)y * L + xn), o_d = __ldg(own + (size_t)yn * L + x);
     const u32 o_u = __ldg(own + (size_t)yp * L + x), o_ur = __ldg(own + (size_t)yp * L + xn);
     const u32 o_l = __ldg(own + (size_t)y * L + xp), o_dl = __ldg(own + (size_t)yn * L + xp);
+    edge_cell(g, s, st, nkey, E, full_compare, lane, y, x, yp, yn, xp, xn, a, o_r, o_d, o_u,
+              o_ur, o_l, o_dl, cnt);
+  }
+  edge_counts(st, lane, cnt);
+}
+
+// L a multiple of 4 (and at least 8): four consecutive cells per thread per
+// step, from one 16-byte load of each of the three rows involved plus the
+// four neighbour cells outside the quad.
+__global__ void __launch_bounds__(EDGES_THREADS) k_edges4(Group g) {
+  const u32 s = blockIdx.y;
+  const u32 L = g.L, L4 = L / 4;
+  const u32 lane = threadIdx.x & 31;
+  SampleState& st = g.st[s];
+  const u32* own = g.owner + (size_t)s * g.LL;
+  const u64* nkey = g.node_key + (size_t)s * g.cap_nodes;
+  Edge* E = g.edges + (size_t)s * g.cap_edges;
+  const bool full_compare = g.k == L;
+  const u32 xsteps = (L4 + blockDim.x - 1) / blockDim.x;
+  u32 cnt[3] = {0, 0, 0};
+  for (u32 y = blockIdx.x; y < L; y += gridDim.x)
+  for (u32 xs = 0; xs < xsteps; ++xs) {
+    const u32 qq = xs * blockDim.x + threadIdx.x;
+    const bool inb = qq < L4;
+    const u32 x0 = inb ? 4 * qq : 0;
+    const u32 yp = y == 0 ? L - 1 : y - 1, yn = y + 1 == L ? 0 : y + 1;
+    const u32 xl = x0 == 0 ? L - 1 : x0 - 1, xr = x0 + 4 == L ? 0 : x0 + 4;
+    const u32* ry = own + (size_t)y * L;
+    const u32* rn = own + (size_t)yn * L;
+    const u32* rp = own + (size_t)yp * L;
+    const uint4 A = __ldg(reinterpret_cast<const uint4*>(ry + x0));
+    const uint4 D = __ldg(reinterpret_cast<const uint4*>(rn + x0));
+    const uint4 U = __ldg(reinterpret_cast<const uint4*>(rp + x0));
+    const u32 a_r = __ldg(ry + xr), a_l = __ldg(ry + xl);
+    const u32 d_l = __ldg(rn + xl), u_r = __ldg(rp + xr);
+    const u32 av[4] = {A.x, A.y, A.z, A.w}, dv[4] = {D.x, D.y, D.z, D.w};
+    const u32 uv[4] = {U.x, U.y, U.z, U.w};
 #pragma unroll
-    for (u32 dir = 0; dir < 2; ++dir) {
-      const u32 by = dir ? yn : y, bx = dir ? x : xn;
-      bool emit = false;
-      u32 b = NONE32, d = 0;
-      u32 kind = 3;  // contact class: 0 both horizontal, 1 both vertical, 2 mixed
-      if (a != NONE32) {
-        b = dir ? o_d : o_r;
-        // owner words carry the k-mer's orientation in bit 31
-        if (b != NONE32 && b != a) kind = (a ^ b) >> 31 ? 2u : a >> 31;
-        if (b != NONE32) {
-          bool internal = false;
-          // the previous contact of the run: one row up (+x edges) or one
-          // column left (+y edges)
-          const bool force = dir == 0 ? (y == 0) : (x == 0);
-          const u32 py = dir == 0 ? yp : y, px = dir == 0 ? x : xp;
-          const u32 qy = dir == 0 ? yp : yn, qx = dir == 0 ? xn : xp;
-          const u32 pa = force ? NONE32 : (dir == 0 ? o_u : o_l);
-          const u32 pb = force ? NONE32 : (dir == 0 ? o_ur : o_dl);
-          const bool same_pair = pa == a && pb == b;
-          if (!same_pair || full_compare) {
-            d = contact_delta(g, s, y, x, by, bx, dir, a & ~OWN_V, b & ~OWN_V, &internal);
-            emit = !internal;
-            if (emit && same_pair) {
-              bool pint = false;
-              const u32 pd = contact_delta(g, s, py, px, qy, qx, dir, pa & ~OWN_V, pb & ~OWN_V,
-                                           &pint);
-              emit = pd != d;
-            }
-          }
-        }
-      }
-      // interspecific-contact counts (Sec. II.A): every contact, before the
-      // run deduplication of the graph edges
-      cnt[0] += kind == 0;
-      cnt[1] += kind == 1;
-      cnt[2] += kind == 2;
-      const u32 mask = __ballot_sync(FULL, emit);
-      if (!mask) continue;
-      u32 basei = 0;
-      const u32 leader = __ffs(mask) - 1;
-      if (lane == leader) basei = atomicAdd(&st.n_edges, (u32)__popc(mask));
-      basei = __shfl_sync(FULL, basei, leader);
-      if (emit) {
-        const u32 e = basei + __popc(mask & ((1u << lane) - 1u));
-        if (e < g.edge_limit) {
-          Edge ed;
-          const u32 ma = a & ~OWN_V, mb = b & ~OWN_V;
-          ed.time = max(nkey[ma], nkey[mb]);
-          ed.m1 = ma;
-          ed.m2 = mb;
-          ed.dxy = d;
-          ed.pad = 0;
-          E[e] = ed;
-        } else {
-          atomicOr(&st.status, ST_EDGE_OVF);
-        }
-      }
+    for (u32 i = 0; i < 4; ++i) {
+      const u32 x = x0 + i;
+      const u32 xp = i == 0 ? xl : x - 1, xn = i == 3 ? xr : x + 1;
+      edge_cell(g, s, st, nkey, E, full_compare, lane, y, x, yp, yn, xp, xn,
+                inb ? av[i] : NONE32, i < 3 ? av[i + 1] : a_r, dv[i], uv[i],
+                i < 3 ? uv[i + 1] : u_r, i > 0 ? av[i - 1] : a_l, i > 0 ? dv[i - 1] : d_l, cnt);
     }
   }
-#pragma unroll
-  for (u32 c = 0; c < 3; ++c) {
-    const u32 t = __reduce_add_sync(FULL, cnt[c]);
-    if (lane == 0 && t)
-      atomicAdd(c == 0 ? &st.contacts_x : c == 1 ? &st.contacts_y : &st.contacts_xy, t);
-  }
+  edge_counts(st, lane, cnt);
 }
 
 // Group one sample's edges by time >> 56 and its node keys by key >> 56
