@@ -281,7 +281,7 @@ class Scheduler:
                     peak_concurrent_batches=int(self.peak_running))
 
 
-class GpuRunner:
+class DeviceRunner:
     """Runs a batch through the C ABI on the worker's own stream with a
     torch-allocated workspace bound to a cached handle."""
 
@@ -345,10 +345,10 @@ def gpu_budget(reserve_frac: float = 0.1, device: int = 0) -> int:
 def make_server(workers: int = 4, budget_bytes: int | None = None, max_batch: int = 256,
                 device: int = 0, journal: str | None = None):
     from . import rsa
-    runner = GpuRunner(workers, device)
+    runner = DeviceRunner(workers, device)
     budget = gpu_budget(device=device) if budget_bytes is None else budget_bytes
     sch = Scheduler(runner, rsa.rsa_workspace_bytes, budget, workers, max_batch, journal=journal)
-    sch.gpu_runner = runner
+    sch.device_runner = runner
     return sch
 
 
@@ -368,7 +368,7 @@ def replay(jobs, workers: int = 4, budget_bytes: int | None = None, time_scale: 
         job.done_event.wait()
     wall = time.perf_counter() - t0
     sch.close()
-    sch.gpu_runner.close()
+    sch.device_runner.close()
     st = sch.stats()
     samples = sum(j.n for j in subs)
     sites = sum(j.n * j.L * j.L for j in subs)

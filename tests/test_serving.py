@@ -113,7 +113,7 @@ def test_served_jobs_alone_and_in_a_mix_match():
     for j in jobs:
         assert j.done_event.wait(120)
     sch.close()
-    sch.gpu_runner.close()
+    sch.device_runner.close()
     for (aj, ac), j in zip(alone, jobs):
         assert j.error is None
         assert np.array_equal(aj, j.nj) and np.array_equal(ac, j.nc)
@@ -191,7 +191,7 @@ def test_served_large_k_jobs_alone_and_in_a_mix_match():
     for j in jobs:
         assert j.done_event.wait(300)
     sch.close()
-    sch.gpu_runner.close()
+    sch.device_runner.close()
     for (aj, ac), j in zip(alone, jobs):
         assert j.error is None
         assert np.array_equal(aj, j.nj) and np.array_equal(ac, j.nc)
