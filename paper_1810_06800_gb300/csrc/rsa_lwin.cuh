@@ -129,6 +129,10 @@ __global__ void __launch_bounds__(NT) k_lwin(Group g, LwinCfg lc, const u32* occ
   const u32 tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 rp = r == 0 ? nc - 1 : r - 1;
   u8* fl = lflag + ((size_t)(s * 2 + F) * L + line) * nc;
+  // a line whose spans are all flagged has no live anchor and final outputs;
+  // every CTA of the cluster reads the same flags (none is written before
+  // the cluster's barriers) and leaves before those barriers
+  if (__all_sync(FULL, lane >= nc || (fl[lane] & 1u) != 0)) return;
   const bool own_dead = (fl[r] & 1u) != 0, prev_dead = (fl[rp] & 1u) != 0;
   const u32 x0 = r * P;
   const u32 q0 = tid * C;   // first cell of this thread's chunk (relative to x0)
