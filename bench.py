@@ -3,7 +3,7 @@
 
 Workload (default): the large-k batch, L = 32768 periodic lattice, k = 4096,
 8 samples with seeds 1..8 per step (per rank under torchrun; rank r uses
-seeds r*8 + 1 ..), 209 GB held on the device.  One step runs the whole path
+seeds r*8 + 1 ..), 78 GB held on the device.  One step runs the whole path
 for the batch: the parallel greedy rounds to jamming (n_j), the contact
 graph, and the first-wrap bisection (n_c).  Prints one JSON line.
 

@@ -91,7 +91,7 @@ def test_l8192_k512_bit_exact_on_stored_seeds():
 
 @pytest.mark.gpu
 def test_l32768_k4096_bit_exact_in_the_benchmark_launch():
-    # the large-k benchmark's launch: seeds 1..8 in one batch (209 GB held on
+    # the large-k benchmark's launch: seeds 1..8 in one batch (78 GB held on
     # the device); every seed with a stored oracle result is compared
     assert _check_against_golden(32768, 4096, list(range(1, 9))) >= 2
 
