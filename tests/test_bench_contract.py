@@ -60,3 +60,33 @@ def test_source_digest_ignores_comments_only(tmp_path, monkeypatch):
     assert b.src_digest("k_tile_cmin") == d0
     f.write_text("int a = 1;\nint b = 3;\n")
     assert b.src_digest("k_tile_cmin") != d0
+
+
+def test_roofline_arithmetic_and_traffic_freshness(tmp_path, monkeypatch):
+    # achieved = byte model x cells processed / summed event time; frac
+    # against the given peak; traffic = the stored bytes per cell x cells per
+    # launch only while the kernel's source digest matches the stored one
+    b = _bench()
+    kst = {"k_lwin_h": (10.0, 2)}                     # 10 ms over 2 launches
+    work = {"raw": [1_000_000_000, 0, 0, 0]}          # cells of the horizontal pass
+    r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0)
+    assert r["alg_bytes_per_cell"] == 16.0 and r["steps"] == ["rowmin"]
+    assert abs(r["achieved"] - 16.0 * 1e9 / 0.010 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 5000.0) < 1e-12
+    assert r["cells_per_launch"] == 5e8 and r["avg_launch_ms"] == 5.0
+    csrc = tmp_path / "paper_1810_06800_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "rsa_lwin.cuh").write_text("int window_pass;\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    entry = {"bytes_per_cell": 2.0, "src": b.src_digest("k_lwin_h")}
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps({"k_lwin_h": entry}))
+    r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0)
+    assert r["traffic"] == 2.0 * 5e8
+    (csrc / "rsa_lwin.cuh").write_text("int window_pass_changed;\n")
+    r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0)
+    assert r["traffic"] is None
+    # no byte model: no fraction
+    r = b.roofline("k_edges", {"k_edges": (3.0, 1)}, work, 1, 64, 4096, 5000.0, "measured",
+                   152, 2070.0)
+    assert r["frac"] is None
