@@ -432,12 +432,15 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
   std::vector<std::pair<int, std::string>> errs(global.size() + 1, {0, ""});
   std::vector<std::thread> workers;
   std::vector<cudaEvent_t> dones;
+  bool setup_failed = false;
   for (size_t g = 0; g < global.size(); ++g) {
     MixSlot* slot = nullptr;
     int rc = mix_slot(dev, global[g].L, global[g].k, &slot);
     if (rc) {
-      cudaEventDestroy(start);
-      return rc;
+      // the shapes already handed to workers still run; join them below
+      errs[g] = {rc, rsa_last_error()};
+      setup_failed = true;
+      break;
     }
     cudaStreamWaitEvent(slot->st, start, 0);
     dones.push_back(slot->done);
@@ -461,7 +464,7 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
       if (rc2) errs[g] = {rc2, rsa_last_error()};
     });
   }
-  if (!small_idx.empty()) {
+  if (!small_idx.empty() && !setup_failed) {
     cudaStream_t sst = nullptr;
     {
       std::lock_guard<std::mutex> lock(g_mix_mu);
