@@ -67,3 +67,40 @@ def wide_keys(L: int, rng_seed: int) -> np.ndarray:
     arr = np.array(special + rest[:n - len(special)], dtype=np.uint64)
     rng.shuffle(arr)
     return arr
+
+
+def two_band_packing() -> np.ndarray:
+    """A jammed packing of k = 4 mers on an L = 40 = 10k torus made of two
+    clusters, the size of the paper's example of a jammed state with several
+    clusters (Sec. III.C).  Returned as horizontal candidate indices y*L + x.
+
+    Along every row the cells with (x - y) mod 40 in {0, 20} stay empty: two
+    diagonal lines that no 4-neighbour step crosses, so they cut the torus
+    into two diagonal bands of 19 cells per row.  In each band an even row
+    holds 4-mers at offsets 1-4, 6-9, 11-14, 16-19 from its diagonal and an
+    odd row at 2-5, 7-10, 12-15, 16-19.  The odd-row 4-mers span the gaps
+    between the even-row 4-mers above and below them, so each band is one
+    cluster, winding once in x and once in y.  No row or column holds more than two free cells in a
+    row, so no 4-mer fits anywhere."""
+    L = 40
+    out = []
+    for y in range(L):
+        starts = (1, 6, 11, 16) if y % 2 == 0 else (2, 7, 12, 16)
+        for band in (0, 20):
+            out.extend(y * L + (y + band + s) % L for s in starts)
+    return np.array(out, dtype=np.uint32)
+
+
+def packing_first_keys(L: int, first: np.ndarray, rng_seed: int) -> np.ndarray:
+    """2 L^2 distinct priorities in which the candidates `first` take the
+    smallest ones (1 .. len(first), in random order) and every other
+    candidate a larger one (random order).  When `first` is a jammed packing
+    the greedy scan accepts exactly it."""
+    rng = np.random.default_rng(rng_seed)
+    n = 2 * L * L
+    first = np.asarray(first, dtype=np.int64)
+    rest = np.setdiff1d(np.arange(n), first)
+    keys = np.empty(n, dtype=np.uint64)
+    keys[first] = rng.permutation(first.size) + 1
+    keys[rest] = rng.permutation(rest.size) + 1 + first.size
+    return keys

@@ -95,3 +95,22 @@ def test_configuration_argument_errors():
     nj2, nc2 = rsa.rsa_results(lat.h, 2)
     assert np.array_equal(nj, nj2) and np.array_equal(nc, nc2)
     lat.close()
+
+
+def test_jammed_state_of_two_clusters():
+    # Sec. III.C: a jammed state may hold several clusters.  Priorities that
+    # put the hand-built two-band packing (k = 4, L = 40) first make it the
+    # jammed state; its two clusters of 160 k-mers both wind along x and y.
+    L, k = 40, 4
+    packing = workloads.two_band_packing()
+    keys = workloads.packing_first_keys(L, packing, 3)
+    lat = rsa.Lattice(L, k)
+    nj, nc = lat.run_keys(keys)
+    wj, wc, _, acc = oracle.sample_keys(L, k, keys)
+    assert (int(nj[0]), int(nc[0])) == (wj, wc) and wj == 320
+    assert np.array_equal(lat.accepted(0), np.sort(packing))
+    got = lat.cluster_sizes(0, 320)
+    assert np.nonzero(got)[0].tolist() == [160] and got[160] == 2
+    assert lat.wrap_dirs(0, 320) == (True, True)
+    _compare(lat, 0, L, k, acc, _ms(320, int(nc[0]), np.random.default_rng(5)))
+    lat.close()

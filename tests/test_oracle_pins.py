@@ -415,3 +415,41 @@ def test_scan_from_seed_equals_scan_of_the_keys(L, k):
         a1, o1 = oracle.scan(L, k, oracle.keys(L, seed))
         a2, o2 = oracle.scan_seed(L, k, seed)
         assert np.array_equal(a1, a2) and np.array_equal(o1, o2)
+
+
+def test_a_jammed_state_can_hold_two_clusters():
+    """Sec. III.C: a jammed state may consist of several clusters (the
+    paper's example is k = 4, L = 10k), though samples in practice end with
+    one.  The two-band packing is built by hand (workloads.two_band_packing):
+    jammed by brute force, two clusters of 160 k-mers by breadth-first
+    search, each winding in both directions (the Proposition).  The oracle's
+    configuration must see the same, and its scan, given priorities that put
+    the packing first, must accept exactly the packing."""
+    L, k = 40, 4
+    acc = workloads.two_band_packing()
+    occ = oracle.occupancy_from_accepted(L, k, acc)
+    cells = [tuple(c) for c in zip(*np.nonzero(occ))]
+    assert acc.size == 320 and len(cells) == 1280          # no overlap
+    assert not brute.viable(L, k, set(cells))              # jammed
+    comps = brute.clusters(L, cells)
+    assert sorted(len(c) for c in comps) == [640, 640]
+    assert all(brute.wrap_dirs(L, c) == (True, True) for c in comps)
+    counts, wx, wy = oracle.configuration(L, k, acc, acc.size)
+    assert np.nonzero(counts)[0].tolist() == [160] and counts[160] == 2
+    assert wx and wy
+    assert oracle.is_jammed(L, k, occ)
+    keys = workloads.packing_first_keys(L, acc, 3)
+    nj, nc, ncp, got = oracle.sample_keys(L, k, keys)
+    assert nj == 320 and np.array_equal(np.sort(got), np.sort(acc))
+    assert 1 <= nc <= nj and nc == ncp == oracle.percolation(L, k, got)[0]
+    assert nc == brute.nc_bruteforce(L, k, got)
+
+
+@pytest.mark.parametrize("L,k,n", [(40, 4, 30), (64, 4, 20), (128, 8, 10), (256, 32, 6)])
+def test_seeded_samples_jam_as_a_single_cluster(L, k, n):
+    # Sec. III.C: in practice the jammed state is one cluster
+    for seed in range(1, n + 1):
+        acc, _ = oracle.scan(L, k, oracle.keys(L, seed))
+        counts, wx, wy = oracle.configuration(L, k, acc, acc.size)
+        assert counts.sum() == 1 and counts[acc.size] == 1, (L, k, seed)
+        assert wx or wy
