@@ -68,7 +68,7 @@ def _load():
     lib.oracle_scan.restype = ctypes.c_int64
     lib.oracle_scan.argtypes = [u32, u32, vp, vp, vp]
     lib.oracle_scan_seed.restype = ctypes.c_int64
-    lib.oracle_scan_seed.argtypes = [u32, u32, u64, vp, vp]
+    lib.oracle_scan_seed.argtypes = [u32, u32, u64, u32, vp, vp]
     lib.oracle_percolation.restype = ctypes.c_int64
     lib.oracle_percolation.argtypes = [u32, u32, vp, ctypes.c_int64, i64p]
     lib.oracle_sample.restype = ctypes.c_int
@@ -124,13 +124,16 @@ def scan(L: int, k: int, key_arr: np.ndarray):
     return acc[:nj].copy(), occ
 
 
-def scan_seed(L: int, k: int, seed: int):
+def scan_seed(L: int, k: int, seed: int, parts: int = 1):
     """scan(L, k, keys(L, seed)) without holding the key array: the largest
-    lattices need only the sort pairs.  Returns (accepted idx, occupancy)."""
+    lattices need only the sort pairs, and with parts > 1 only those of one
+    key range at a time (about 32 GB / parts at L = 32768, every key hashed
+    parts + 1 times).  Returns (accepted idx, occupancy)."""
     _check_lk(L, k)
     acc = np.empty(L * L // k + 1, dtype=np.uint32)
     occ = np.empty((L, L), dtype=np.uint8)
-    nj = _load().oracle_scan_seed(L, k, seed & (2**64 - 1), acc.ctypes.data, occ.ctypes.data)
+    nj = _load().oracle_scan_seed(L, k, seed & (2**64 - 1), max(1, int(parts)), acc.ctypes.data,
+                                  occ.ctypes.data)
     if nj < 0:
         raise MemoryError("oracle_scan_seed failed")
     return acc[:nj].copy(), occ

@@ -82,17 +82,15 @@ static void orc_cell(uint32_t L, uint32_t idx, uint32_t i, uint32_t *y, uint32_t
     else        { *y = (y0 + i) % L; *x = x0; }
 }
 
-/* Scan n = 2L^2 (key, idx) pairs already sorted by key, accepting a
- * candidate iff its k cells are free.  accepted[] receives the accepted idx
- * in scan order.  Returns n_j, or -1 if two keys are equal (the order would
+/* Continue the scan over n (key, idx) pairs already sorted by key: accept a
+ * candidate iff its k cells are free in occ, appending accepted idx to
+ * accepted[*nj ..].  Returns 0, or -1 if two keys are equal (the order would
  * be undefined). */
-static int64_t orc_scan_sorted(uint32_t L, uint32_t k, const orc_pair *p, uint64_t n,
-                               uint32_t *accepted, uint8_t *occ)
+static int orc_scan_more(uint32_t L, uint32_t k, const orc_pair *p, uint64_t n,
+                         uint32_t *accepted, int64_t *nj, uint8_t *occ)
 {
     for (uint64_t i = 1; i < n; ++i)
         if (p[i].key == p[i - 1].key) return -1;
-    memset(occ, 0, (size_t)L * L);
-    int64_t nj = 0;
     for (uint64_t s = 0; s < n; ++s) {
         uint32_t idx = p[s].idx, y, x, i, ok = 1;
         for (i = 0; i < k && ok; ++i) {
@@ -104,8 +102,20 @@ static int64_t orc_scan_sorted(uint32_t L, uint32_t k, const orc_pair *p, uint64
             orc_cell(L, idx, i, &y, &x);
             occ[(size_t)y * L + x] = 1;
         }
-        accepted[nj++] = idx;
+        accepted[(*nj)++] = idx;
     }
+    return 0;
+}
+
+/* Scan n = 2L^2 (key, idx) pairs already sorted by key from an empty
+ * lattice.  accepted[] receives the accepted idx in scan order.  Returns
+ * n_j, or -1 if two keys are equal. */
+static int64_t orc_scan_sorted(uint32_t L, uint32_t k, const orc_pair *p, uint64_t n,
+                               uint32_t *accepted, uint8_t *occ)
+{
+    int64_t nj = 0;
+    memset(occ, 0, (size_t)L * L);
+    if (orc_scan_more(L, k, p, n, accepted, &nj, occ)) return -1;
     return nj;
 }
 
@@ -125,31 +135,52 @@ int64_t oracle_scan(uint32_t L, uint32_t k, const uint64_t *keys,
 }
 
 /* The same scan for the seeded priorities of oracle_keys, for the largest
- * lattices (L = 32768: 2^31 pairs, 34 GB): no separate key array, and the
- * sort is split by the top 16 bits of the key -- a counting pass, each pair
- * written straight into its bucket, then each bucket sorted by itself -- so
- * no temporary as large as the pairs is needed. */
-int64_t oracle_scan_seed(uint32_t L, uint32_t k, uint64_t seed, uint32_t *accepted,
-                         uint8_t *occ)
+ * lattices (L = 32768: 2^31 candidates): no key array is kept.  The top 16
+ * bits of a key name its bucket (65536 buckets, in key order); a counting
+ * pass gives each bucket's size.  The buckets are then taken in `parts`
+ * consecutive runs, lowest keys first: for each run every key is generated
+ * again and those of the run's buckets are written straight into their
+ * bucket, each bucket is sorted by itself, and the run is scanned, the
+ * lattice carrying over from the run before.  Only one run's pairs are held
+ * (16 bytes x about 2L^2 / parts). */
+int64_t oracle_scan_seed(uint32_t L, uint32_t k, uint64_t seed, uint32_t parts,
+                         uint32_t *accepted, uint8_t *occ)
 {
     const uint64_t n = 2ULL * L * L, b = oracle_base(seed), NB = 65536;
-    uint64_t *at = (uint64_t *)calloc(NB + 1, sizeof(uint64_t));
-    orc_pair *p = (orc_pair *)malloc(n * sizeof(orc_pair));
-    if (!at || !p) { free(at); free(p); return -2; }
-    for (uint64_t i = 0; i < n; ++i) at[(oracle_key(b, i) >> 48) + 1] += 1;
-    for (uint64_t j = 0; j < NB; ++j) at[j + 1] += at[j];   /* bucket starts */
-    for (uint64_t i = 0; i < n; ++i) {
-        uint64_t key = oracle_key(b, i);
-        orc_pair *q = &p[at[key >> 48]++];                    /* next slot of its bucket */
-        q->key = key;
-        q->idx = (uint32_t)i;
+    if (parts < 1) parts = 1;
+    if (parts > NB) parts = (uint32_t)NB;
+    uint64_t *start = (uint64_t *)calloc(NB + 1, sizeof(uint64_t));
+    uint64_t *at = (uint64_t *)malloc(NB * sizeof(uint64_t));
+    if (!start || !at) { free(start); free(at); return -2; }
+    for (uint64_t i = 0; i < n; ++i) start[(oracle_key(b, i) >> 48) + 1] += 1;
+    for (uint64_t j = 0; j < NB; ++j) start[j + 1] += start[j];  /* bucket starts */
+    uint64_t most = 0;                                          /* largest run */
+    for (uint64_t q = 0; q < parts; ++q) {
+        uint64_t lo = q * NB / parts, hi = (q + 1) * NB / parts;
+        if (start[hi] - start[lo] > most) most = start[hi] - start[lo];
     }
-    /* at[j] is now the end of bucket j (the start of bucket j + 1) */
-    for (uint64_t j = 0, lo = 0; j < NB; lo = at[j], ++j)
-        if (at[j] - lo > 1) qsort(p + lo, at[j] - lo, sizeof(orc_pair), orc_cmp);
-    int64_t nj = orc_scan_sorted(L, k, p, n, accepted, occ);
+    orc_pair *p = (orc_pair *)malloc((most ? most : 1) * sizeof(orc_pair));
+    if (!p) { free(start); free(at); return -2; }
+    memset(occ, 0, (size_t)L * L);
+    int64_t nj = 0;
+    for (uint64_t q = 0; q < parts; ++q) {
+        const uint64_t lo = q * NB / parts, hi = (q + 1) * NB / parts, off = start[lo];
+        for (uint64_t j = lo; j < hi; ++j) at[j] = start[j] - off;  /* write cursors */
+        for (uint64_t i = 0; i < n; ++i) {
+            uint64_t key = oracle_key(b, i), j = key >> 48;
+            if (j < lo || j >= hi) continue;
+            orc_pair *r = &p[at[j]++];
+            r->key = key;
+            r->idx = (uint32_t)i;
+        }
+        for (uint64_t j = lo; j < hi; ++j)
+            if (start[j + 1] - start[j] > 1)
+                qsort(p + (start[j] - off), start[j + 1] - start[j], sizeof(orc_pair), orc_cmp);
+        if (orc_scan_more(L, k, p, start[hi] - off, accepted, &nj, occ)) { nj = -1; break; }
+    }
     free(p);
     free(at);
+    free(start);
     return nj;
 }
 

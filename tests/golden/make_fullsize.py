@@ -18,10 +18,13 @@ Only oracle/ is called; nothing here reads the CUDA library.
   python tests/golden/make_fullsize.py --case 8192,512 --seeds 1-8
   python tests/golden/make_fullsize.py --case 32768,4096 --seeds 1 --out part1.json
   python tests/golden/make_fullsize.py --merge part1.json part2.json
+  python tests/golden/make_fullsize.py --case 32768,4096 --seeds 4 --parts 16 --out p4.json
 
 Entries already in the file are kept, so runs can be split and resumed;
 --out writes to another file (one process per sample, several at once, on a
 host with room for them), and --merge adds such files' entries here.
+--parts splits the oracle's sort into key ranges handled one at a time, so
+that an L = 32768 sample holds about 2 GB of sort pairs instead of 34 GB.
 """
 from __future__ import annotations
 
@@ -49,12 +52,12 @@ def parse_seeds(s: str):
     return out
 
 
-def one(L: int, k: int, seed: int) -> dict:
+def one(L: int, k: int, seed: int, parts: int = 1) -> dict:
     import numpy as np
 
     import oracle
     t0 = time.perf_counter()
-    acc, occ = oracle.scan_seed(L, k, seed)
+    acc, occ = oracle.scan_seed(L, k, seed, parts)
     del occ
     nc, ncp = oracle.percolation(L, k, acc)
     srt = np.sort(acc).astype("<u4")
@@ -93,6 +96,8 @@ def main() -> int:
     ap.add_argument("--seeds", help="e.g. 1-8 or 1,2,5")
     ap.add_argument("--out", default=OUT, help="file to add the entries to")
     ap.add_argument("--merge", nargs="*", help="add the entries of these files")
+    ap.add_argument("--parts", type=int, default=1,
+                    help="split the oracle's sort into this many key ranges (less memory)")
     args = ap.parse_args()
     if args.merge:
         db = load(OUT)
@@ -108,7 +113,7 @@ def main() -> int:
         key = f"{L},{k},{seed}"
         if key in db["samples"]:
             continue
-        rec = one(L, k, seed)
+        rec = one(L, k, seed, args.parts)
         rec["host"] = f"{platform.machine()}, {os.cpu_count()} cores"
         db["samples"][key] = rec
         save(db, out)

@@ -410,11 +410,14 @@ def test_horizontal_wrapping_probability_at_pc():
 @pytest.mark.parametrize("L,k", [(1, 1), (5, 2), (16, 3), (64, 4), (128, 64), (300, 17)])
 def test_scan_from_seed_equals_scan_of_the_keys(L, k):
     # the seeded scan forms its (key, idx) pairs from the key function itself;
-    # it must accept exactly what the scan of the materialised keys accepts
+    # it must accept exactly what the scan of the materialised keys accepts,
+    # however many key ranges it is split into (one bucket per range at
+    # 65536; larger counts are clamped to that)
     for seed in (1, 7, 123456789):
         a1, o1 = oracle.scan(L, k, oracle.keys(L, seed))
-        a2, o2 = oracle.scan_seed(L, k, seed)
-        assert np.array_equal(a1, a2) and np.array_equal(o1, o2)
+        for parts in (1, 2, 7, 64) + ((65536, 10**6) if L <= 16 else ()):
+            a2, o2 = oracle.scan_seed(L, k, seed, parts)
+            assert np.array_equal(a1, a2) and np.array_equal(o1, o2), parts
 
 
 def test_a_jammed_state_can_hold_two_clusters():
