@@ -2,7 +2,7 @@
 
 The oracle (sequential priority-order scan, Sec. II.B; union-find with
 displacement vectors, Sec. II.C and II.D) needs minutes per sample at
-L = 8192 and about half an hour per sample at L = 32768, so its results for
+L = 8192 and over an hour per sample at L = 32768, so its results for
 these samples are stored in tests/golden/fullsize.json by
 tests/golden/make_fullsize.py, a script that calls only oracle/.  Each GPU
 run here is the benchmark's own launch shape (all seeds of the batch in one
@@ -45,7 +45,7 @@ def _stored(L, k):
 
 def test_golden_file_covers_the_full_size_workloads():
     assert len(_stored(8192, 512)) >= 8
-    assert len(_stored(32768, 4096)) >= 2
+    assert len(_stored(32768, 4096)) >= 8
 
 
 def test_golden_records_match_the_live_oracle_on_a_small_case():
@@ -93,7 +93,7 @@ def test_l8192_k512_bit_exact_on_stored_seeds():
 def test_l32768_k4096_bit_exact_in_the_benchmark_launch():
     # the large-k benchmark's launch: seeds 1..8 in one batch (78 GB held on
     # the device); every seed with a stored oracle result is compared
-    assert _check_against_golden(32768, 4096, list(range(1, 9))) >= 2
+    assert _check_against_golden(32768, 4096, list(range(1, 9))) >= 8
 
 
 @pytest.mark.gpu
