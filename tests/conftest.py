@@ -8,9 +8,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# the autotuner's cache of this test session: a fresh file, not the user's
-os.environ.setdefault("RSA_TUNE_CACHE",
-                      os.path.join(tempfile.mkdtemp(prefix="rsa_tune_"), "tune.jsonl"))
+# the autotuner's cache of this test session: a fresh file, not the user's,
+# removed when the session ends
+if "RSA_TUNE_CACHE" not in os.environ:
+    import atexit
+    import shutil
+    _tune_dir = tempfile.mkdtemp(prefix="rsa_tune_")
+    atexit.register(shutil.rmtree, _tune_dir, True)
+    os.environ["RSA_TUNE_CACHE"] = os.path.join(_tune_dir, "tune.jsonl")
 
 
 def pytest_configure(config):
