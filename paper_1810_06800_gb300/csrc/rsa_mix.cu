@@ -233,7 +233,7 @@ rsa_tune_t default_config(uint32_t L, uint32_t k) {
   } else {
     c.mode = RSA_MODE_GLOBAL;
     c.rounds_per_check = 4;
-    c.window_threads = 256;
+    c.window_threads = 0;  // the handle's own default
   }
   return c;
 }
@@ -421,7 +421,7 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
       }
     } else {
       global.push_back(Job{gkv.first.first, gkv.first.second, c.rounds_per_check ? c.rounds_per_check : 4u,
-                           c.window_threads ? c.window_threads : 256u, &gkv.second});
+                           c.window_threads, &gkv.second});
     }
   }
   // everything already queued on the caller's stream comes first
@@ -453,7 +453,7 @@ extern "C" int rsa_run_mix(const uint32_t* L, const uint32_t* k, const uint64_t*
       std::vector<uint32_t> a(m), b(m);
       for (uint32_t i = 0; i < m; ++i) sd[i] = seeds[(*J.idx)[i]];
       int rc2 = rsa_set_rounds_per_check(slot->h, J.rpc);
-      if (rsa_set_window_threads(slot->h, J.wt)) rsa_set_window_threads(slot->h, 256);
+      if (rsa_set_window_threads(slot->h, J.wt)) rsa_set_window_threads(slot->h, 0);
       if (!rc2) rc2 = rsa_run_seeds(slot->h, sd.data(), m, slot->st);
       if (!rc2) rc2 = rsa_results(slot->h, a.data(), b.data(), m);
       if (!rc2) cudaEventRecord(slot->done, slot->st);
