@@ -19,8 +19,9 @@
 // (L is a multiple of k, so the blocks tile the torus): the window of cell x
 // in block b at offset j is the suffix minimum of block b-1 from offset j+1
 // and the prefix minimum of block b up to j (the whole of block b if
-// j = k-1).  A line is cut into nc = L / P spans of P = 256 C cells, one CTA
-// each, launched as one thread-block cluster per line.  Thread t holds the C
+// j = k-1).  A line is cut into nc = L / P spans of P = NT C cells (NT = 256
+// threads, or 128 with C = 32 on 4096-cell spans), one CTA each, launched as
+// one thread-block cluster per line.  Thread t holds the C
 // consecutive candidates of its chunk in registers: liveness from the staged
 // occupancy words (a candidate is live iff the next occupied cell is at
 // least k ahead), splitmix64 priorities of the live ones, in-chunk prefix and
