@@ -157,7 +157,7 @@ int rsa_set_rounds_per_check(rsa_t *h, uint32_t rounds);
 /* CTA size of the long-k window pass of later runs on this handle: 256 or
  * 128 threads per CTA, each thread then holding twice as many cells of the
  * span; 0 restores the default (128 on the argmin-offset long-k path with
- * 4096-cell spans, 256 otherwise).  128 needs the argmin-offset long-k path
+ * 4096-cell spans and k >= 512, 256 otherwise).  128 needs the argmin-offset long-k path
  * with spans of 2048 or 4096 cells (RSA_EINVAL otherwise).  Results do not
  * depend on it. */
 int rsa_set_window_threads(rsa_t *h, uint32_t threads);

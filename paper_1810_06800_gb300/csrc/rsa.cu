@@ -475,10 +475,10 @@ cudaError_t launch_lwin(rsa_t* h, Group g, const Geometry& G, const u32* occw, c
 }
 
 // Default CTA size of the long-k window pass: 128 threads x 32 cells on
-// 4096-cell spans (measured 3% faster than 256 x 16 at L = 8192, k = 512 and
-// L = 32768, k = 4096), 256 threads elsewhere.
-u32 default_window_threads(const Geometry& G) {
-  return G.lw && G.lw_cfg.P == 4096 ? 128u : 256u;
+// 4096-cell spans with k >= 512 (measured 3% faster than 256 x 16 at
+// L = 8192, k = 512 and L = 32768, k = 4096), 256 threads elsewhere.
+u32 default_window_threads(const Geometry& G, u32 k) {
+  return G.lw && G.lw_cfg.P == 4096 && k >= 512 ? 128u : 256u;
 }
 
 int launch_check(const char* what) {
@@ -940,7 +940,7 @@ int rsa_create(uint32_t L, uint32_t k, uint64_t seed, rsa_t** out) {
   h->k = k;
   h->seed = seed;
   h->geo = plan(L, k);
-  h->lw_threads = default_window_threads(h->geo);
+  h->lw_threads = default_window_threads(h->geo, k);
   *out = h;
   g_err.clear();
   return 0;
@@ -1137,7 +1137,7 @@ int rsa_set_rounds_per_check(rsa_t* h, uint32_t rounds) {
 
 int rsa_set_window_threads(rsa_t* h, uint32_t threads) {
   if (!h) return fail(RSA_EINVAL, "null handle");
-  if (threads == 0) threads = default_window_threads(h->geo);
+  if (threads == 0) threads = default_window_threads(h->geo, h->k);
   if (threads != 256 && threads != 128) return fail(RSA_EINVAL, "window CTA size must be 128 or 256");
   if (threads == 128 && !(h->geo.lw && (h->geo.lw_cfg.P == 4096 || h->geo.lw_cfg.P == 2048)))
     return fail(RSA_EINVAL, "128-thread windows need the long-k offset path with spans of 2048 or 4096 cells");
