@@ -85,3 +85,33 @@ def test_product_path_never_touches_the_oracle():
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "import paper_1810_06800_gb300" not in txt, f
             assert "from paper_1810_06800_gb300" not in txt and "librsa_gb300" not in txt, f
+
+
+def test_host_settings_validate_on_the_cpu(lib):
+    # handle settings are host-side checks: 128-thread window CTAs need the
+    # argmin-offset long-k path with 2048- or 4096-cell spans; 0 restores the
+    # shape's default; rounds per check must be 1 .. 64
+    from paper_1810_06800_gb300 import rsa
+    for L, k, ok128 in [(32768, 4096, True), (8192, 512, True), (4096, 64, True),
+                        (2048, 256, True), (1024, 32, False), (1024, 64, False),
+                        (100, 3, False), (4096, 3500, False)]:
+        h = rsa.rsa_create(L, k, 1)
+        try:
+            if ok128:
+                rsa.rsa_set_window_threads(h, 128)
+            else:
+                with pytest.raises(rsa.RSAError) as e:
+                    rsa.rsa_set_window_threads(h, 128)
+                assert e.value.code == rsa.RSA_EINVAL
+            rsa.rsa_set_window_threads(h, 256)
+            rsa.rsa_set_window_threads(h, 0)
+            for bad in (64, 512, 1):
+                with pytest.raises(rsa.RSAError):
+                    rsa.rsa_set_window_threads(h, bad)
+            rsa.rsa_set_rounds_per_check(h, 1)
+            rsa.rsa_set_rounds_per_check(h, 64)
+            for bad in (0, 65):
+                with pytest.raises(rsa.RSAError):
+                    rsa.rsa_set_rounds_per_check(h, bad)
+        finally:
+            rsa.rsa_destroy(h)
