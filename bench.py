@@ -269,7 +269,7 @@ def sample_text(wl_name, L, k, m, secs, threads):
     return (f"{m} seeded samples of L={Lo}, k={ko} (the same L/k) in {secs:.1f} s on "
             f"{threads} threads, scaled by the sites ratio ({L}/{Lo})^2 = {scale:.0f} to "
             f"samples of L={L}, k={k}; one oracle sample of the workload itself takes "
-            f"minutes (4572 s on one x86 core at L=32768, k=4096), so the scaled rate "
+            f"minutes (4017-6247 s on one x86 core at L=32768, k=4096), so the scaled rate "
             f"overstates the oracle's full-size speed")
 
 
