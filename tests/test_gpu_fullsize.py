@@ -48,6 +48,29 @@ def test_golden_file_covers_the_full_size_workloads():
     assert len(_stored(32768, 4096)) >= 8
 
 
+def test_stored_full_size_samples_against_table1():
+    # Table I (Sec. III.A; tests/golden/table1.txt): k = 512 (n = 9) and
+    # k = 4096 (n = 12) at L = 100k.  The stored samples are at L/k = 16 and
+    # 8, so the finite-size offsets of Eqs. (pcscaling), (pjscaling) allow
+    # the same loose bands as the smaller Table I smoke test; every sample
+    # has n_c <= n_j, and the paper's > 2k wrap test gives the same n_c
+    # (L >= 3k + 2)
+    table = {}
+    with open(os.path.join(HERE, "golden", "table1.txt")) as f:
+        for line in f:
+            line = line.split("#")[0].split()
+            if line:
+                table[int(line[0])] = (float(line[1]), float(line[2]))
+    for L, k, n in [(8192, 512, 9), (32768, 4096, 12)]:
+        recs = list(_stored(L, k).values())
+        nj = np.array([r["n_j"] for r in recs], dtype=float)
+        nc = np.array([r["n_c"] for r in recs], dtype=float)
+        assert np.all(nc <= nj) and all(r["n_c_paper"] == r["n_c"] for r in recs)
+        want_pc, want_pj = table[n]
+        assert abs(k * nj.mean() / L**2 - want_pj) < 0.012, (L, k)
+        assert abs(k * nc.mean() / L**2 - want_pc) < 0.05, (L, k)
+
+
 def test_golden_records_match_the_live_oracle_on_a_small_case():
     # the stored format (counts and digest) reproduces from the oracle itself
     rec = _stored(256, 32)[1]
