@@ -128,8 +128,10 @@ unsigned long long rsa_mix_launches(void);
 /* How a shape runs: RSA_MODE_SMALL (one CTA per sample, `threads` per CTA)
  * or RSA_MODE_GLOBAL (the tiled / long-k / general kernels over the whole
  * batch, `rounds_per_check` greedy rounds per captured graph chunk and host
- * check, `window_threads` threads per CTA of the long-k window pass).
- * ms_per_sample is the time measured when the choice was made. */
+ * check, `window_threads` threads per CTA of the long-k window pass, 0 for
+ * the handle's default as rsa_set_window_threads(h, 0) gives it).
+ * ms_per_sample is the time measured when the choice was made (0 for an
+ * unmeasured default). */
 #define RSA_MODE_GLOBAL 0
 #define RSA_MODE_SMALL 1
 typedef struct {
