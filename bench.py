@@ -309,10 +309,13 @@ def run_reference(args, wl, world, rank):
     return 0
 
 
-def roofline(dom, kstats, work, passes, L, n_cells_round, hbm_peak, peak_kind, sm_count, sm_mhz):
+def roofline(dom, kstats, work, passes, L, n_cells_round, hbm_peak, peak_kind, sm_count, sm_mhz,
+             window_threads=0):
     """Roofline of kernel `dom` over the profiled pass: algorithmic bytes per
     processed cell (KERNEL_STEPS) times the cells its launches processed,
-    over its summed CUDA-event time, against the measured copy bandwidth."""
+    over its summed CUDA-event time, against the measured copy bandwidth.
+    `window_threads` is the window-pass CTA size the run asked for (0: the
+    library's default, not known here)."""
     dom_ms, dom_launches = kstats[dom]
     if dom in WORK_CELLS:
         ctr, share = WORK_CELLS[dom]
@@ -333,7 +336,8 @@ def roofline(dom, kstats, work, passes, L, n_cells_round, hbm_peak, peak_kind, s
                alg_bytes_per_launch=alg / dom_launches,
                avg_launch_ms=dom_ms / dom_launches)
     # measured DRAM bytes per launch, scaled from the ncu capture's bytes per
-    # cell; null once the kernel's source file has changed since the capture
+    # cell; null once the kernel's source file has changed since the capture,
+    # or when the capture names a window-pass CTA size the run did not ask for
     traffic_db = {}
     tp = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tp):
@@ -341,6 +345,8 @@ def roofline(dom, kstats, work, passes, L, n_cells_round, hbm_peak, peak_kind, s
             traffic_db = json.load(f)
     ent = traffic_db.get(dom)
     fresh = bool(ent) and ent.get("src") == src_digest(dom)
+    if fresh and "window_threads" in ent:
+        fresh = ent["window_threads"] == window_threads
     out["traffic"] = (ent["bytes_per_cell"] * cells / dom_launches) if fresh else None
     if dom in OPS_PER_CELL:
         keys = work["raw"][TILE_KEYS[dom]]
@@ -684,12 +690,14 @@ def main():
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     sm_mhz = float(json.load(open(pk))["sm_max_mhz"]) if os.path.exists(pk) else 2070.0
-    roof = roofline(dom, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz)
+    roof = roofline(dom, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz,
+                    args.window_threads)
     # the same figures for every round kernel with a byte model
     roof_all = {}
     for nm in ours:
         if nm in KERNEL_STEPS:
-            r = roofline(nm, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz)
+            r = roofline(nm, ours, work, passes, L, L * L, hbm_peak, peak_kind, sm_count, sm_mhz,
+                         args.window_threads)
             roof_all[nm] = {k2: r.get(k2) for k2 in ("achieved", "frac", "alg_bytes_per_cell",
                                                       "avg_launch_ms", "traffic")}
     total_ms = sum(x[0] for x in ours.values())

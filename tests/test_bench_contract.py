@@ -83,8 +83,16 @@ def test_roofline_arithmetic_and_traffic_freshness(tmp_path, monkeypatch):
     (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps({"k_lwin_h": entry}))
     r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0)
     assert r["traffic"] == 2.0 * 5e8
+    # a capture of one window-pass CTA size counts only for runs that ask for it
+    entry["window_threads"] = 256
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps({"k_lwin_h": entry}))
+    r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0, 256)
+    assert r["traffic"] == 2.0 * 5e8
+    for asked in (0, 128):
+        r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0, asked)
+        assert r["traffic"] is None
     (csrc / "rsa_lwin.cuh").write_text("int window_pass_changed;\n")
-    r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0)
+    r = b.roofline("k_lwin_h", kst, work, 0, 0, 0, 5000.0, "measured", 152, 2070.0, 256)
     assert r["traffic"] is None
     # no byte model: no fraction
     r = b.roofline("k_edges", {"k_edges": (3.0, 1)}, work, 1, 64, 4096, 5000.0, "measured",
